@@ -1,0 +1,212 @@
+/*
+ * p2s.h -- C ABI of libp2s, a GB300 (sm_103a) implementation of the per-frame
+ * synthesis path of the phase-to-space (P2S) turbulence simulator
+ * (Mao, Chimitt & Chan, "Accelerating Atmospheric Turbulence Simulation via
+ * Learned Phase-to-Space Transform", ICCV 2021).
+ *
+ * The path, per frame (Sec. 3, Fig. 3 and Fig. 8):
+ *   1. correlated Zernike coefficients on an anchor grid, by Fourier filtering
+ *      of counter-based white noise and colouring with chol(R_Z)  (Sec. 2.2, 3.4)
+ *   2. bilinear interpolation of the coefficients to every pixel   (Sec. 3.4)
+ *   3. the tilt modes alpha_2, alpha_3 as a sub-pixel backward warp (Sec. 2.2, 3.3)
+ *   4. the P2S network alpha_{4..36} -> beta in R^K                 (Sec. 3.3)
+ *   5. the basis blur y = sum_k h_k * (beta_k . x_w)                (Sec. 3.1, Eq. 3-5)
+ *
+ * Conventions shared by every call:
+ *   - Images are NHWC float32, rows contiguous, C in {1, 3}.  Device pointers
+ *     unless the call says "host".  The caller owns every buffer it passes;
+ *     an output must not alias an input.
+ *   - Work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t;
+ *     NULL = the legacy default stream) and runs asynchronously; the call
+ *     returns once it is enqueued.  Host arrays passed in are read before the
+ *     call returns.
+ *   - No C++ exception crosses the ABI.  Every call returns a p2s_status;
+ *     on P2S_EINVAL nothing is enqueued and no output is written.
+ *     p2s_last_error() gives a one-line reason for the last failure on the
+ *     calling thread.
+ *   - A context is used by one host thread at a time (or externally locked).
+ */
+#ifndef P2S_H
+#define P2S_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct p2s_ctx p2s_ctx;
+
+typedef enum {
+    P2S_OK = 0,
+    P2S_EINVAL = 1,       /* bad argument or shape; nothing was enqueued       */
+    P2S_ENOMEM = 2,       /* device or host allocation failed                  */
+    P2S_ECUDA = 3,        /* a CUDA runtime call failed                        */
+    P2S_ETIMEOUT = 4,     /* a bounded device wait gave up (status word set)   */
+    P2S_EBUSY = 5,        /* serving queue or HBM budget full; retry later     */
+    P2S_EUNSUPPORTED = 6  /* valid request this build or device cannot serve   */
+} p2s_status;
+
+/* Arithmetic of the network and the basis contraction.  Fields and warp are
+ * FP32 in every mode; the tap accumulation is FP32 in every mode. */
+typedef enum {
+    P2S_FP32 = 0,    /* FP32 throughout (CUDA cores)                          */
+    P2S_BF16 = 1,    /* BF16 tensor-core operands, FP32 accumulation          */
+    P2S_FP8E4M3 = 2, /* E4M3 contraction operands with per-basis scales       */
+    P2S_FP16 = 3     /* FP16 tensor-core operands, FP32 accumulation          */
+} p2s_precision;
+
+/* Which PSF a tap uses (Sec. 3.1):
+ *   SCATTER  y_c[p + o(t)] += G[p, t] x_c[p]   source pixel's PSF, y = sum_k h_k * (beta_k . x)
+ *   GATHER   y_c[q] += G[q, t] x_c[q - o(t)]   output pixel's PSF, Eq. 5
+ *   FFT      the scatter form evaluated by batched FFTs (comparison variant)
+ * with G[p, t] = sum_k beta[p, k] H[k, t] and o(t) = (ty - taps_h/2, tx - taps_w/2). */
+typedef enum { P2S_SCATTER = 0, P2S_GATHER = 1, P2S_FFT = 2 } p2s_blur_form;
+
+/* PSF basis (Eq. 4): K row vectors of taps_h x taps_w taps, host, row-major
+ * [K][taps_h * taps_w], copied by p2s_create.  taps_h, taps_w odd. */
+typedef struct {
+    const double *H;
+    int K;
+    int taps_h;
+    int taps_w;
+} p2s_basis;
+
+/* P2S network (Sec. 3.3): n_layers fully connected layers, ReLU after every
+ * layer but the last.  dims[0] = 33 (alpha_4..alpha_36), dims[n_layers] = K.
+ * W[l] is host row-major [dims[l+1]][dims[l]], b[l] is [dims[l+1]]; copied. */
+typedef struct {
+    int n_layers;
+    const int *dims;
+    const double *const *W;
+    const double *const *b;
+} p2s_mlp;
+
+/* Spatial correlation of the anchor fields (Sec. 3.4; the paper's Takato
+ * formulas are not printed, this is the stated Gaussian reading):
+ *   anchors every `anchor_spacing` pixels, A = floor((H-1)/s) + 2 per axis;
+ *   torus of the next power of two >= A + guard per axis;
+ *   covariance exp(-|d|^2 / (2 ell^2)) (d in pixels) wrapped on the torus;
+ *   n_kernels = 1 (shared) or 7 (one per radial order 1..7), lengths in
+ *   corr_len_px (host, copied); fft_guard < 0 selects ceil(3 max(ell) / s).
+ * kappa converts tilt coefficients to pixels (d = kappa (alpha_3, alpha_2)
+ * in (row, column)); 0 selects -4/pi, the value for PSFs sampled with 2x
+ * zero padding of the pupil. */
+typedef struct {
+    int anchor_spacing;
+    int n_kernels;
+    const double *corr_len_px;
+    int fft_guard;
+    double kappa;
+} p2s_corr_params;
+
+/* One frame: device NHWC float32, rows contiguous (row pitch W*C floats). */
+typedef struct {
+    float *data;
+    int H;
+    int W;
+    int C;
+} p2s_image;
+
+/* Derived sizes for a frame shape, see p2s_geometry_of. */
+typedef struct {
+    int anchors_h, anchors_w;  /* anchor grid                                 */
+    int torus_h, torus_w;      /* FFT torus of the field filter               */
+    int alpha_stride;          /* floats per anchor in alpha buffers (36)     */
+} p2s_geometry;
+
+/* Create a simulator.  Copies the basis and weights to the device (converted
+ * to the requested precision), builds R_Z for J = 2..36 and its Cholesky
+ * factor in FP64 (Sec. 2.2), and the field filter tables.  Runs on the
+ * current CUDA device.  Errors: EINVAL on inconsistent shapes (dims[0] != 33,
+ * dims[last] != K, even taps, spacing < 1, n_kernels not 1 or 7); ENOMEM;
+ * EUNSUPPORTED if the (precision, form) pair is not built for this device. */
+p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr_params *corr,
+                      p2s_precision precision, p2s_blur_form form, p2s_ctx **out);
+
+/* Release everything the context owns.  Waits for its own streams. NULL is a no-op. */
+void p2s_destroy(p2s_ctx *ctx);
+
+const char *p2s_status_string(p2s_status s);
+const char *p2s_last_error(void);
+
+/* Anchor and torus sizes of an H x W frame under this context's parameters. */
+p2s_status p2s_geometry_of(const p2s_ctx *ctx, int H, int W, p2s_geometry *out);
+
+/* The whole path (steps 1-5) on n frames.  frames[i] and out[i] must have the
+ * same H, W, C; frames may differ in size.  d_over_r0 and seeds are host
+ * arrays of n entries: D/r0 of frame i (> 0) and its Philox key.  Frame i's
+ * result depends only on (frames[i], d_over_r0[i], seeds[i]) and the
+ * context.  Scratch is owned by the context and grown on demand. */
+p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                        const unsigned long long *seeds, const p2s_image *out, void *stream);
+
+/* As p2s_simulate, but frames[i].data and out[i].data are HOST pointers: the
+ * call stages them through device buffers owned by the context (host->device
+ * copy, path, device->host copy, all on `stream`) and returns when out[] is
+ * written.  Pinned host memory gives full copy bandwidth. */
+p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                             const unsigned long long *seeds, const p2s_image *out, void *stream);
+
+/* ---- stage entry points: each step alone, for per-stage parity ---------- */
+
+/* Step 1a: the white noise of stream (seed, mode), F_h x F_w row-major into
+ * `out` (device float32), sample i from Philox4x32-10 counter (i/4, mode, 0, 0)
+ * word i%4, key (seed mod 2^32, seed >> 32), Box-Muller per word pair. */
+p2s_status p2s_stage_noise(p2s_ctx *ctx, unsigned long long seed, int mode, int torus_h, int torus_w,
+                           float *out, void *stream);
+
+/* Steps 1a-1c for n frames of size H x W: alpha on the anchors, device
+ * float32 [n][anchors_h][anchors_w][36]; slot 0 is piston (written 0), slot
+ * j-1 holds Noll mode j = 2..36.  Host arrays d_over_r0[n], seeds[n]. */
+p2s_status p2s_stage_fields(p2s_ctx *ctx, int H, int W, int n, const float *d_over_r0,
+                            const unsigned long long *seeds, float *alpha, void *stream);
+
+/* Steps 2-3: x_w = warp of `in` by the tilts of `alpha` (one frame, the
+ * layout of p2s_stage_fields), into `out` (same shape as in). */
+p2s_status p2s_stage_warp(p2s_ctx *ctx, const p2s_image *in, const float *alpha, const p2s_image *out,
+                          void *stream);
+
+/* Steps 2 + 4: beta of every pixel of an H x W frame from `alpha` (one
+ * frame), device float32 [H][W][K], in the context's precision. */
+p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *beta, void *stream);
+
+/* Step 5 alone: y = blur of x_w with per-pixel weights beta (device float32
+ * [H][W][K]) in the context's form and precision (beta is rounded to the
+ * operand type first). */
+p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, const p2s_image *out,
+                          void *stream);
+
+/* ---- kernel timing ------------------------------------------------------- */
+
+/* Per-kernel totals recorded while profiling is on: CUDA events bracket every
+ * launch of the library on the stream it is launched on.  flops and bytes
+ * are the launch's ALGORITHMIC work (what the method needs, not what the
+ * hardware moved), summed over launches. */
+typedef struct {
+    char name[48];
+    int launches;
+    double total_ms;
+    double flops;
+    double bytes;
+} p2s_kernel_stat;
+
+/* enable = 1 clears the record and starts recording; 0 stops. */
+p2s_status p2s_profile(p2s_ctx *ctx, int enable);
+
+/* Waits for the recorded events and writes up to max_stats aggregated entries
+ * (one per kernel name, in order of first launch); *n_stats gets the count. */
+p2s_status p2s_profile_read(p2s_ctx *ctx, p2s_kernel_stat *stats, int max_stats, int *n_stats);
+
+/* ---- host-side building blocks ----------------------------------------- */
+
+/* Noll covariance R_Z of modes J = 2..j_max at D/r0 = 1 (Sec. 2.2; closed
+ * form of Noll 1976), FP64 row-major [(j_max-1)^2] into host `out`.
+ * j_max in [3, 66].  Pure host code; needs no GPU. */
+p2s_status p2s_noll_covariance(int j_max, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P2S_H */

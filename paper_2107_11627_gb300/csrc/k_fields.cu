@@ -1,0 +1,296 @@
+// Anchor-grid Zernike fields (Sec. 3.4): counter-based white noise, Fourier
+// filtering on the torus, inter-mode colouring by chol(R_Z) (Sec. 2.2).
+//
+// The filter sqrt(C) of the wrapped Gaussian covariance is separable, so the
+// 2-D filtering is a batch of 1-D circular filters along rows, then along
+// columns.  Each 1-D filter is FFT -> real gain -> inverse FFT in shared
+// memory, with two real rows packed into one complex sequence (the gain is
+// real and even, so the two results come back in the real and imaginary
+// parts).  Only the A_w columns of the row pass and the A_h rows of the
+// column pass that the anchors use are kept.
+#include <stdint.h>
+
+#include "p2s_internal.h"
+
+namespace p2s {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kFftElems = 4096;  // complex elements per ping-pong buffer
+
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the two 32x32->64-bit
+// multiplies, key bumped by the Weyl constants after every round.
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// -2 ln u for u = (w + 1/2) 2^-32, accurate near u = 1 through log1p of 1 - u.
+__device__ __forceinline__ float neg2log_u(uint32_t w) {
+    const float two_m32 = 2.3283064365386963e-10f;
+    if (w < 0x80000000u) return -2.0f * logf(((float)w + 0.5f) * two_m32);
+    const float v = ((float)(0xFFFFFFFFu - w) + 0.5f) * two_m32;
+    return -2.0f * log1pf(-v);
+}
+
+// Box-Muller pair from two words: r = sqrt(-2 ln u_a), angle 2 pi u_b.  The
+// quadrant comes exactly from the top two bits of w_b, the rest through sincospi.
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float *z0, float *z1) {
+    const float r = sqrtf(neg2log_u(wa));
+    const float x = ((float)(wb & 0x3FFFFFFFu) + 0.5f) * 4.656612873077393e-10f;  // (0, 1/2)
+    float sn, cs;
+    sincospif(x, &sn, &cs);
+    float c, s;
+    switch (wb >> 30) {
+        case 0: c = cs; s = sn; break;
+        case 1: c = -sn; s = cs; break;
+        case 2: c = -cs; s = -sn; break;
+        default: c = sn; s = -cs; break;
+    }
+    *z0 = r * c;
+    *z1 = r * s;
+}
+
+// Four normals of quad q of stream (seed, mode).
+__device__ __forceinline__ void normals4(unsigned long long seed, int mode, uint32_t q, float z[4]) {
+    U4 w = philox4x32_10(U4{q, (uint32_t)mode, 0u, 0u}, (uint32_t)seed, (uint32_t)(seed >> 32));
+    box_muller(w.x, w.y, &z[0], &z[1]);
+    box_muller(w.z, w.w, &z[2], &z[3]);
+}
+
+__global__ void noise_kernel(unsigned long long seed, int mode, long long n, float *out) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * q >= n) return;
+    float z[4];
+    normals4(seed, mode, (uint32_t)q, z);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (4 * q + i < n) out[4 * q + i] = z[i];
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Radix-2 Stockham FFT of R rows of length N (power of two) held in `a`,
+// ping-ponging with `b`; natural order in and out.  All threads take part.
+// Returns the buffer that holds the result.  tw[m] = exp(-2 pi i m / N).
+__device__ float2 *fft_rows(float2 *a, float2 *b, const float2 *tw, int N, int R, bool inverse) {
+    const int half = N >> 1;
+    for (int ns = 1; ns < N; ns <<= 1) {
+        const int tstep = N / (2 * ns);
+        for (int idx = threadIdx.x; idx < R * half; idx += blockDim.x) {
+            const int r = idx / half, j = idx - r * half;
+            const int k = j & (ns - 1);
+            const float2 v0 = a[r * N + j];
+            float2 w = tw[k * tstep];
+            if (inverse) w.y = -w.y;
+            const float2 v1 = cmul(a[r * N + j + half], w);
+            const int d = ((j - k) << 1) + k;
+            b[r * N + d] = make_float2(v0.x + v1.x, v0.y + v1.y);
+            b[r * N + d + ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+        }
+        __syncthreads();
+        float2 *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Row pass: white noise rows (y0, y0+1) packed as one complex row, filtered
+// along x; columns [0, Aw) of both rows go to t[frame][mode][y][x].
+__global__ void __launch_bounds__(kThreads) row_filter_kernel(FrameBatch fb, int Fh, int Fw, int Aw, int rows_per_cta,
+                                                              const float2 *__restrict__ tw,
+                                                              const float *__restrict__ gain,
+                                                              const int *__restrict__ kernel_of_mode, float *t) {
+    extern __shared__ float2 smem[];
+    const int mode = blockIdx.y, frame = blockIdx.z;
+    const int R = rows_per_cta;  // complex rows = row pairs
+    float2 *buf0 = smem, *buf1 = smem + R * Fw, *stw = smem + 2 * R * Fw;
+    float *sg = (float *)(stw + (Fw / 2 > 0 ? Fw / 2 : 1));
+    const float *g = gain + (size_t)kernel_of_mode[mode] * Fw;
+    for (int i = threadIdx.x; i < Fw / 2; i += blockDim.x) stw[i] = tw[i];
+    for (int i = threadIdx.x; i < Fw; i += blockDim.x) sg[i] = g[i];
+    const int y_base = blockIdx.x * R * 2;  // first torus row of this CTA
+    const int n_rows = min(2 * R, Fh - y_base);
+    const unsigned long long seed = fb.seed[frame];
+    // noise: samples [y_base*Fw, (y_base+n_rows)*Fw) of stream (seed, mode), quad by quad
+    const int q0 = (y_base * Fw) >> 2, q1 = ((y_base + n_rows) * Fw + 3) >> 2;
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        float z[4];
+        normals4(seed, mode, (uint32_t)q, z);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int s = 4 * q + i - y_base * Fw;
+            if (s < 0 || s >= n_rows * Fw) continue;
+            const int row = s / Fw, x = s - row * Fw;
+            float *dst = (float *)&buf0[(row >> 1) * Fw + x];
+            dst[row & 1] = z[i];
+        }
+    }
+    if (n_rows & 1)  // odd tail (Fh is a power of two, so only when Fh == 1)
+        for (int x = threadIdx.x; x < Fw; x += blockDim.x) buf0[(n_rows >> 1) * Fw + x].y = 0.0f;
+    __syncthreads();
+    const int Rk = (n_rows + 1) >> 1;
+    float2 *res = fft_rows(buf0, buf1, stw, Fw, Rk, false);
+    for (int i = threadIdx.x; i < Rk * Fw; i += blockDim.x) {
+        const float gg = sg[i % Fw];
+        res[i].x *= gg;
+        res[i].y *= gg;
+    }
+    __syncthreads();
+    float2 *other = res == buf0 ? buf1 : buf0;
+    res = fft_rows(res, other, stw, Fw, Rk, true);
+    float *tf = t + ((size_t)frame * kModes + mode) * Fh * Aw;
+    for (int i = threadIdx.x; i < n_rows * Aw; i += blockDim.x) {
+        const int row = i / Aw, x = i - row * Aw;
+        const float2 v = res[(row >> 1) * Fw + x];
+        tf[(size_t)(y_base + row) * Aw + x] = (row & 1) ? v.y : v.x;
+    }
+}
+
+// Column pass: columns (x0, x0+1) of t packed as one complex column, filtered
+// along y; rows [0, Ah) go to f[frame][mode][y][x].
+__global__ void __launch_bounds__(kThreads) col_filter_kernel(int Fh, int Ah, int Aw, int cols_per_cta,
+                                                              const float2 *__restrict__ tw,
+                                                              const float *__restrict__ gain,
+                                                              const int *__restrict__ kernel_of_mode,
+                                                              const float *__restrict__ t, float *f) {
+    extern __shared__ float2 smem[];
+    const int mode = blockIdx.y, frame = blockIdx.z;
+    const int R = cols_per_cta;
+    float2 *buf0 = smem, *buf1 = smem + R * Fh, *stw = smem + 2 * R * Fh;
+    float *sg = (float *)(stw + (Fh / 2 > 0 ? Fh / 2 : 1));
+    const float *g = gain + (size_t)kernel_of_mode[mode] * Fh;
+    for (int i = threadIdx.x; i < Fh / 2; i += blockDim.x) stw[i] = tw[i];
+    for (int i = threadIdx.x; i < Fh; i += blockDim.x) sg[i] = g[i];
+    const int x_base = blockIdx.x * R * 2;
+    const int n_cols = min(2 * R, Aw - x_base);
+    const int Rk = (n_cols + 1) >> 1;
+    const float *tf = t + ((size_t)frame * kModes + mode) * Fh * Aw;
+    for (int i = threadIdx.x; i < Rk * Fh; i += blockDim.x) {
+        const int c = i / Fh, y = i - c * Fh;
+        const int x = x_base + 2 * c;
+        const float re = tf[(size_t)y * Aw + x];
+        const float im = (2 * c + 1 < n_cols) ? tf[(size_t)y * Aw + x + 1] : 0.0f;
+        buf0[c * Fh + y] = make_float2(re, im);
+    }
+    __syncthreads();
+    float2 *res = fft_rows(buf0, buf1, stw, Fh, Rk, false);
+    for (int i = threadIdx.x; i < Rk * Fh; i += blockDim.x) {
+        const float gg = sg[i % Fh];
+        res[i].x *= gg;
+        res[i].y *= gg;
+    }
+    __syncthreads();
+    float2 *other = res == buf0 ? buf1 : buf0;
+    res = fft_rows(res, other, stw, Fh, Rk, true);
+    float *ff = f + ((size_t)frame * kModes + mode) * Ah * Aw;
+    for (int i = threadIdx.x; i < n_cols * Ah; i += blockDim.x) {
+        const int cc = i / Ah, y = i - cc * Ah;
+        const float2 v = res[(cc >> 1) * Fh + y];
+        ff[(size_t)y * Aw + x_base + cc] = (cc & 1) ? v.y : v.x;
+    }
+}
+
+// alpha(a) = (D/r0)^(5/6) L f(a): slot 0 (piston) = 0, slot l+1 = mode l + 2.
+__global__ void colour_kernel(FrameBatch fb, int A, const float *__restrict__ L, const float *__restrict__ f,
+                              float *alpha) {
+    __shared__ float sL[kModes * kModes];
+    for (int i = threadIdx.x; i < kModes * kModes; i += blockDim.x) sL[i] = L[i];
+    __syncthreads();
+    const int frame = blockIdx.y;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A) return;
+    const float *ff = f + (size_t)frame * kModes * A + a;
+    float v[kModes];
+#pragma unroll
+    for (int l = 0; l < kModes; ++l) v[l] = ff[(size_t)l * A];
+    const float sc = fb.scale[frame];
+    float *out = alpha + ((size_t)frame * A + a) * kAlphaStride;
+    out[0] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kModes; ++j) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int l = 0; l <= j; ++l) acc = fmaf(sL[j * kModes + l], v[l], acc);
+        out[j + 1] = sc * acc;
+    }
+}
+
+}  // namespace
+
+p2s_status launch_noise(unsigned long long seed, int mode, int Fh, int Fw, float *out, cudaStream_t st) {
+    const long long n = (long long)Fh * Fw;
+    const long long quads = (n + 3) / 4;
+    noise_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, st>>>(seed, mode, n, out);
+    P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+size_t fields_scratch_bytes(const FieldGeom &g, int n) {
+    const size_t t = (size_t)n * kModes * g.Fh * g.Aw * sizeof(float);
+    const size_t f = (size_t)n * kModes * g.Ah * g.Aw * sizeof(float);
+    return ((t + 255) & ~(size_t)255) + f;
+}
+
+p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb, float *alpha, void *scratch,
+                         cudaStream_t st) {
+    if (fb.n <= 0) return P2S_OK;
+    const FilterTable *th = nullptr, *tw = nullptr;
+    p2s_status s = filter_table(ctx, g.Fh, &th);
+    if (s != P2S_OK) return s;
+    if ((s = filter_table(ctx, g.Fw, &tw)) != P2S_OK) return s;
+    float *t = (float *)scratch;
+    const size_t t_bytes = (size_t)fb.n * kModes * g.Fh * g.Aw * sizeof(float);
+    float *f = (float *)((char *)scratch + ((t_bytes + 255) & ~(size_t)255));
+
+    // rows: R row pairs per CTA, R * Fw <= kFftElems
+    int R = kFftElems / g.Fw;
+    if (R < 1) R = 1;
+    if (R > (g.Fh + 1) / 2) R = (g.Fh + 1) / 2;
+    size_t smem = (size_t)2 * R * g.Fw * sizeof(float2) + (size_t)(g.Fw / 2 > 0 ? g.Fw / 2 : 1) * sizeof(float2) +
+                  (size_t)g.Fw * sizeof(float);
+    P2S_CUDA(cudaFuncSetAttribute(row_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid_r((g.Fh + 2 * R - 1) / (2 * R), kModes, fb.n);
+    ProfScope pr(ctx, st, "fields_row_filter", 0.0, (double)fb.n * kModes * g.Fh * g.Aw * 4);
+    row_filter_kernel<<<grid_r, kThreads, smem, st>>>(fb, g.Fh, g.Fw, g.Aw, R, tw->twiddle, tw->gain,
+                                                       ctx->d_kernel_of_mode, t);
+    P2S_CUDA(cudaGetLastError());
+
+    int Rc = kFftElems / g.Fh;
+    if (Rc < 1) Rc = 1;
+    if (Rc > (g.Aw + 1) / 2) Rc = (g.Aw + 1) / 2;
+    smem = (size_t)2 * Rc * g.Fh * sizeof(float2) + (size_t)(g.Fh / 2 > 0 ? g.Fh / 2 : 1) * sizeof(float2) +
+           (size_t)g.Fh * sizeof(float);
+    P2S_CUDA(cudaFuncSetAttribute(col_filter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid_c((g.Aw + 2 * Rc - 1) / (2 * Rc), kModes, fb.n);
+    ProfScope pc(ctx, st, "fields_col_filter", 0.0,
+                 (double)fb.n * kModes * (g.Fh * g.Aw + g.Ah * g.Aw) * 4);
+    col_filter_kernel<<<grid_c, kThreads, smem, st>>>(g.Fh, g.Ah, g.Aw, Rc, th->twiddle, th->gain,
+                                                       ctx->d_kernel_of_mode, t, f);
+    P2S_CUDA(cudaGetLastError());
+
+    const int A = g.Ah * g.Aw;
+    dim3 grid_a((A + 127) / 128, fb.n);
+    ProfScope pa(ctx, st, "fields_colour", (double)fb.n * A * kModes * (kModes + 1),
+                 (double)fb.n * A * (kModes + kAlphaStride) * 4);
+    colour_kernel<<<grid_a, 128, 0, st>>>(fb, A, ctx->d_L, f, alpha);
+    P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+}  // namespace p2s

@@ -1,0 +1,629 @@
+// Host side of libp2s: the C ABI, context set-up in FP64, validation, dispatch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "p2s_internal.h"
+
+namespace p2s {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+static p2s_status einval(const char *msg) {
+    set_error("%s", msg);
+    return P2S_EINVAL;
+}
+
+// ---- Noll modes and covariance (Sec. 2.2; closed form of Noll 1976) --------
+
+// Radial order n and |m| of Noll mode j (j >= 1): modes of order n occupy
+// j in (n(n+1)/2, (n+1)(n+2)/2]; |m| grows along the order, each m > 0 twice.
+static void noll_nm(int j, int *n, int *m) {
+    int order = 0;
+    while ((order + 1) * (order + 2) / 2 < j) ++order;
+    int pos = j - order * (order + 1) / 2 - 1;
+    *n = order;
+    *m = (order % 2 == 0) ? 2 * ((pos + 1) / 2) : 2 * (pos / 2) + 1;
+}
+
+static double noll_entry(int i, int j) {
+    int ni, mi, nj, mj;
+    noll_nm(i, &ni, &mi);
+    noll_nm(j, &nj, &mj);
+    if (mi != mj) return 0.0;
+    if (mi != 0 && ((i - j) % 2) != 0) return 0.0;
+    const double kc = std::tgamma(14.0 / 3.0) * std::pow(24.0 / 5.0 * std::tgamma(6.0 / 5.0), 5.0 / 6.0) *
+                      std::tgamma(11.0 / 6.0) * std::tgamma(11.0 / 6.0) / (2.0 * M_PI * M_PI);
+    const int e = (ni + nj - 2 * mi) / 2;
+    const double sign = (e % 2 == 0) ? 1.0 : -1.0;
+    const double num = std::tgamma((ni + nj - 5.0 / 3.0) / 2.0);
+    const double den = std::tgamma((ni - nj + 17.0 / 3.0) / 2.0) * std::tgamma((nj - ni + 17.0 / 3.0) / 2.0) *
+                       std::tgamma((ni + nj + 23.0 / 3.0) / 2.0);
+    return kc * sign * std::sqrt((ni + 1.0) * (nj + 1.0)) * num / den;
+}
+
+// In-place lower Cholesky factor of an n x n SPD matrix (row-major).
+static bool cholesky(double *a, int n) {
+    for (int j = 0; j < n; ++j) {
+        double d = a[j * n + j];
+        for (int k = 0; k < j; ++k) d -= a[j * n + k] * a[j * n + k];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        a[j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = a[i * n + j];
+            for (int k = 0; k < j; ++k) v -= a[i * n + k] * a[j * n + k];
+            a[i * n + j] = v / d;
+        }
+        for (int k = j + 1; k < n; ++k) a[j * n + k] = 0.0;
+    }
+    return true;
+}
+
+static int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+p2s_status geometry(const p2s_ctx *ctx, int H, int W, FieldGeom *g) {
+    if (H < 1 || W < 1) return einval("frame must be at least 1 x 1");
+    g->H = H;
+    g->W = W;
+    g->s = ctx->s;
+    g->Ah = (H - 1) / ctx->s + 2;
+    g->Aw = (W - 1) / ctx->s + 2;
+    g->Fh = next_pow2(g->Ah + ctx->guard);
+    g->Fw = next_pow2(g->Aw + ctx->guard);
+    if (g->Fh > 4096 || g->Fw > 4096) {
+        set_error("filter torus %dx%d exceeds 4096 (raise anchor_spacing)", g->Fh, g->Fw);
+        return P2S_EUNSUPPORTED;
+    }
+    return P2S_OK;
+}
+
+// Separable filter of the wrapped Gaussian covariance on a torus of length F:
+// c1[d] = sum_m exp(-(d + mF)^2 s^2 / (2 ell^2)), C1 = DFT(c1) (real, > 0 by
+// Poisson summation), gain = sqrt(C1) / F.  sqrt(C2) = gain_h (x) gain_w.
+p2s_status filter_table(p2s_ctx *ctx, int F, const FilterTable **out) {
+    auto it = ctx->tables.find(F);
+    if (it != ctx->tables.end()) {
+        *out = &it->second;
+        return P2S_OK;
+    }
+    FilterTable t;
+    t.F = F;
+    std::vector<float2> tw(F / 2 > 0 ? F / 2 : 1);
+    for (int m = 0; m < F / 2; ++m) {
+        double a = 2.0 * M_PI * m / F;
+        tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    std::vector<float> gain((size_t)ctx->n_kernels * F);
+    std::vector<double> c1(F);
+    for (int kk = 0; kk < ctx->n_kernels; ++kk) {
+        const double ell = ctx->ell[kk], s = ctx->s;
+        const int M = (int)std::ceil(40.0 * ell / (s * F)) + 1;
+        for (int d = 0; d < F; ++d) {
+            double acc = 0.0;
+            for (int m = -M; m <= M; ++m) {
+                double x = (d + (double)m * F) * s;
+                acc += std::exp(-x * x / (2.0 * ell * ell));
+            }
+            c1[d] = acc;
+        }
+        for (int u = 0; u < F; ++u) {
+            double acc = 0.0;
+            for (int d = 0; d < F; ++d) acc += c1[d] * std::cos(2.0 * M_PI * (double)((long long)u * d % F) / F);
+            gain[(size_t)kk * F + u] = (float)(std::sqrt(acc > 0.0 ? acc : 0.0) / F);
+        }
+    }
+    P2S_CUDA(cudaMalloc(&t.twiddle, tw.size() * sizeof(float2)));
+    P2S_CUDA(cudaMalloc(&t.gain, gain.size() * sizeof(float)));
+    P2S_CUDA(cudaMemcpy(t.twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(t.gain, gain.data(), gain.size() * sizeof(float), cudaMemcpyHostToDevice));
+    auto res = ctx->tables.emplace(F, t);
+    *out = &res.first->second;
+    return P2S_OK;
+}
+
+static cudaEvent_t pool_event(p2s_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(const p2s_ctx *ctx, cudaStream_t st, const char *name, double flops, double bytes)
+    : ctx_(const_cast<p2s_ctx *>(ctx)), st_(st) {
+    if (!ctx_ || !ctx_->profiling) return;
+    ProfRecord r{name, pool_event(ctx_), pool_event(ctx_), flops, bytes};
+    if (!r.start || !r.stop) return;
+    cudaEventRecord(r.start, st_);
+    ctx_->prof.push_back(r);
+    idx_ = (int)ctx_->prof.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (idx_ >= 0) cudaEventRecord(ctx_->prof[idx_].stop, st_);
+}
+
+static int radial_order(int j) {
+    int n, m;
+    noll_nm(j, &n, &m);
+    return n;
+}
+
+}  // namespace p2s
+
+using namespace p2s;
+
+extern "C" {
+
+const char *p2s_status_string(p2s_status s) {
+    switch (s) {
+        case P2S_OK: return "ok";
+        case P2S_EINVAL: return "invalid argument";
+        case P2S_ENOMEM: return "out of memory";
+        case P2S_ECUDA: return "CUDA error";
+        case P2S_ETIMEOUT: return "device wait timed out";
+        case P2S_EBUSY: return "busy";
+        case P2S_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *p2s_last_error(void) { return g_err; }
+
+p2s_status p2s_noll_covariance(int j_max, double *out) {
+    if (!out || j_max < 3 || j_max > 66) return einval("j_max must be in [3, 66] and out non-NULL");
+    const int n = j_max - 1;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) out[a * n + b] = noll_entry(a + 2, b + 2);
+    return P2S_OK;
+}
+
+p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr_params *corr,
+                      p2s_precision precision, p2s_blur_form form, p2s_ctx **out) {
+    if (!out) return einval("out is NULL");
+    *out = nullptr;
+    if (!basis || !mlp || !corr) return einval("basis, mlp and corr must be non-NULL");
+    if (!basis->H || basis->K < 1 || basis->K > 128) return einval("basis: need H and 1 <= K <= 128");
+    if (basis->taps_h < 1 || basis->taps_w < 1 || basis->taps_h % 2 == 0 || basis->taps_w % 2 == 0)
+        return einval("basis taps must be odd and positive");
+    if (basis->taps_h > 33 || basis->taps_w > 33) {
+        set_error("taps larger than 33 x 33 are not built");
+        return P2S_EUNSUPPORTED;
+    }
+    if (mlp->n_layers < 1 || !mlp->dims || !mlp->W || !mlp->b) return einval("mlp: need n_layers >= 1, dims, W, b");
+    if (mlp->dims[0] != kHiModes) return einval("mlp: dims[0] must be 33 (alpha_4..alpha_36)");
+    if (mlp->dims[mlp->n_layers] != basis->K) return einval("mlp: last width must equal K");
+    for (int l = 0; l < mlp->n_layers; ++l) {
+        if (mlp->dims[l + 1] < 1 || !mlp->W[l] || !mlp->b[l]) return einval("mlp: bad layer");
+        if (mlp->dims[l + 1] > 128) {
+            set_error("network widths above 128 are not built");
+            return P2S_EUNSUPPORTED;
+        }
+    }
+    if (corr->anchor_spacing < 1) return einval("anchor_spacing must be >= 1");
+    if (corr->n_kernels != 1 && corr->n_kernels != 7) return einval("n_kernels must be 1 or 7");
+    if (!corr->corr_len_px) return einval("corr_len_px is NULL");
+    for (int k = 0; k < corr->n_kernels; ++k)
+        if (!(corr->corr_len_px[k] > 0.0) || !std::isfinite(corr->corr_len_px[k])) return einval("corr_len_px must be > 0");
+    if (!(form == P2S_SCATTER || form == P2S_GATHER || form == P2S_FFT)) return einval("unknown blur form");
+    if (!(precision == P2S_FP32 || precision == P2S_BF16 || precision == P2S_FP16 || precision == P2S_FP8E4M3))
+        return einval("unknown precision");
+    if (precision != P2S_FP32 || form == P2S_FFT) {
+        set_error("precision/form pair not built yet");
+        return P2S_EUNSUPPORTED;
+    }
+
+    p2s_ctx *ctx = new (std::nothrow) p2s_ctx();
+    if (!ctx) return P2S_ENOMEM;
+    auto fail = [&](p2s_status st) {
+        p2s_destroy(ctx);
+        return st;
+    };
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        set_error("no CUDA device");
+        return fail(P2S_ECUDA);
+    }
+    ctx->prec = precision;
+    ctx->form = form;
+    ctx->K = basis->K;
+    ctx->th = basis->taps_h;
+    ctx->tw = basis->taps_w;
+    ctx->T = ctx->th * ctx->tw;
+    ctx->H.assign(basis->H, basis->H + (size_t)ctx->K * ctx->T);
+    ctx->n_layers = mlp->n_layers;
+    ctx->dims.assign(mlp->dims, mlp->dims + mlp->n_layers + 1);
+    for (int l = 0; l < mlp->n_layers; ++l) {
+        const int fi = ctx->dims[l], fo = ctx->dims[l + 1];
+        ctx->W.emplace_back(mlp->W[l], mlp->W[l] + (size_t)fi * fo);
+        ctx->b.emplace_back(mlp->b[l], mlp->b[l] + fo);
+    }
+    ctx->s = corr->anchor_spacing;
+    ctx->n_kernels = corr->n_kernels;
+    ctx->ell.assign(corr->corr_len_px, corr->corr_len_px + corr->n_kernels);
+    double ell_max = 0.0;
+    for (double e : ctx->ell) ell_max = e > ell_max ? e : ell_max;
+    ctx->guard = corr->fft_guard >= 0 ? corr->fft_guard : (int)std::ceil(3.0 * ell_max / ctx->s);
+    ctx->kappa = corr->kappa != 0.0 ? corr->kappa : -4.0 / M_PI;
+    for (int l = 0; l < kModes; ++l) ctx->kernel_of_mode[l] = ctx->n_kernels == 1 ? 0 : radial_order(l + 2) - 1;
+
+    // R_Z (J = 2..36) and its Cholesky factor, FP64.
+    std::vector<double> R(kModes * kModes);
+    for (int a = 0; a < kModes; ++a)
+        for (int c = 0; c < kModes; ++c) R[a * kModes + c] = noll_entry(a + 2, c + 2);
+    if (!cholesky(R.data(), kModes)) {
+        set_error("R_Z is not positive definite");
+        return fail(P2S_EINVAL);
+    }
+    std::vector<float> Lf(kModes * kModes);
+    for (int i = 0; i < kModes * kModes; ++i) Lf[i] = (float)R[i];
+
+    // FP32 device copies used by the plain path.
+    std::vector<float> H32(ctx->H.begin(), ctx->H.end()), Ht32((size_t)ctx->T * ctx->K);
+    for (int k = 0; k < ctx->K; ++k)
+        for (int t = 0; t < ctx->T; ++t) Ht32[(size_t)t * ctx->K + k] = (float)ctx->H[(size_t)k * ctx->T + t];
+    if (cudaMalloc(&ctx->d_L, Lf.size() * 4) != cudaSuccess || cudaMalloc(&ctx->d_H32, H32.size() * 4) != cudaSuccess ||
+        cudaMalloc(&ctx->d_Ht32, Ht32.size() * 4) != cudaSuccess ||
+        cudaMalloc(&ctx->d_kernel_of_mode, sizeof ctx->kernel_of_mode) != cudaSuccess) {
+        set_error("device allocation failed in p2s_create");
+        return fail(P2S_ENOMEM);
+    }
+    if (cudaMemcpy(ctx->d_L, Lf.data(), Lf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_H32, H32.data(), H32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_Ht32, Ht32.data(), Ht32.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_kernel_of_mode, ctx->kernel_of_mode, sizeof ctx->kernel_of_mode, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        set_error("upload failed in p2s_create");
+        return fail(P2S_ECUDA);
+    }
+    for (int l = 0; l < ctx->n_layers; ++l) {
+        const int fi = ctx->dims[l], fo = ctx->dims[l + 1];
+        std::vector<float> wt((size_t)fi * fo), bb(fo);
+        for (int o = 0; o < fo; ++o) {
+            for (int i = 0; i < fi; ++i) wt[(size_t)i * fo + o] = (float)ctx->W[l][(size_t)o * fi + i];
+            bb[o] = (float)ctx->b[l][o];
+        }
+        float *dw = nullptr, *db = nullptr;
+        if (cudaMalloc(&dw, wt.size() * 4) != cudaSuccess || cudaMalloc(&db, bb.size() * 4) != cudaSuccess) {
+            cudaFree(dw);
+            set_error("device allocation failed in p2s_create");
+            return fail(P2S_ENOMEM);
+        }
+        ctx->d_Wt32.push_back(dw);
+        ctx->d_b32.push_back(db);
+        if (cudaMemcpy(dw, wt.data(), wt.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(db, bb.data(), bb.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("upload failed in p2s_create");
+            return fail(P2S_ECUDA);
+        }
+    }
+    // Keep stream-ordered scratch cached between calls.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+        unsigned long long thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = ctx;
+    return P2S_OK;
+}
+
+void p2s_destroy(p2s_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    for (auto &r : ctx->prof) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    cudaFree(ctx->d_L);
+    cudaFree(ctx->d_H32);
+    cudaFree(ctx->d_Ht32);
+    cudaFree(ctx->d_kernel_of_mode);
+    for (float *p : ctx->d_Wt32) cudaFree(p);
+    for (float *p : ctx->d_b32) cudaFree(p);
+    for (auto &kv : ctx->tables) {
+        cudaFree(kv.second.twiddle);
+        cudaFree(kv.second.gain);
+    }
+    cudaFree(ctx->tc.d_W);
+    cudaFree(ctx->tc.d_H);
+    cudaFree(ctx->tc.d_bias);
+    delete ctx;
+}
+
+p2s_status p2s_profile(p2s_ctx *ctx, int enable) {
+    if (!ctx) return einval("ctx is NULL");
+    if (enable) {
+        for (auto &r : ctx->prof) {
+            ctx->event_pool.push_back(r.start);
+            ctx->event_pool.push_back(r.stop);
+        }
+        ctx->prof.clear();
+    }
+    ctx->profiling = enable != 0;
+    return P2S_OK;
+}
+
+p2s_status p2s_profile_read(p2s_ctx *ctx, p2s_kernel_stat *stats, int max_stats, int *n_stats) {
+    if (!ctx || !n_stats || (max_stats > 0 && !stats)) return einval("bad profile_read arguments");
+    std::vector<p2s_kernel_stat> agg;
+    for (auto &r : ctx->prof) {
+        P2S_CUDA(cudaEventSynchronize(r.stop));
+        float ms = 0.0f;
+        P2S_CUDA(cudaEventElapsedTime(&ms, r.start, r.stop));
+        size_t i = 0;
+        for (; i < agg.size(); ++i)
+            if (std::strncmp(agg[i].name, r.name, sizeof agg[i].name) == 0) break;
+        if (i == agg.size()) {
+            p2s_kernel_stat z;
+            std::memset(&z, 0, sizeof z);
+            std::snprintf(z.name, sizeof z.name, "%s", r.name);
+            agg.push_back(z);
+        }
+        agg[i].launches += 1;
+        agg[i].total_ms += ms;
+        agg[i].flops += r.flops;
+        agg[i].bytes += r.bytes;
+    }
+    *n_stats = (int)agg.size();
+    for (int i = 0; i < (int)agg.size() && i < max_stats; ++i) stats[i] = agg[i];
+    return P2S_OK;
+}
+
+p2s_status p2s_geometry_of(const p2s_ctx *ctx, int H, int W, p2s_geometry *out) {
+    if (!ctx || !out) return einval("ctx and out must be non-NULL");
+    FieldGeom g;
+    p2s_status st = geometry(ctx, H, W, &g);
+    if (st != P2S_OK) return st;
+    out->anchors_h = g.Ah;
+    out->anchors_w = g.Aw;
+    out->torus_h = g.Fh;
+    out->torus_w = g.Fw;
+    out->alpha_stride = kAlphaStride;
+    return P2S_OK;
+}
+
+// ---- stage entry points ----------------------------------------------------
+
+p2s_status p2s_stage_noise(p2s_ctx *ctx, unsigned long long seed, int mode, int torus_h, int torus_w, float *out,
+                           void *stream) {
+    if (!ctx || !out) return einval("ctx and out must be non-NULL");
+    if (mode < 0 || torus_h < 1 || torus_w < 1 || (long long)torus_h * torus_w > (1ll << 30))
+        return einval("bad noise shape or mode");
+    return launch_noise(seed, mode, torus_h, torus_w, out, (cudaStream_t)stream);
+}
+
+static p2s_status check_frames_meta(int n, const float *d_over_r0, const unsigned long long *seeds) {
+    if (n < 0) return einval("n must be >= 0");
+    if (n > 0 && (!d_over_r0 || !seeds)) return einval("d_over_r0 and seeds must be non-NULL");
+    for (int i = 0; i < n; ++i)
+        if (!(d_over_r0[i] > 0.0f) || !std::isfinite(d_over_r0[i])) return einval("D/r0 must be finite and > 0");
+    return P2S_OK;
+}
+
+static void fill_batch(FrameBatch *fb, int n, const float *d_over_r0, const unsigned long long *seeds) {
+    fb->n = n;
+    for (int i = 0; i < n; ++i) {
+        fb->seed[i] = seeds[i];
+        fb->scale[i] = (float)std::pow((double)d_over_r0[i], 5.0 / 6.0);
+    }
+}
+
+p2s_status p2s_stage_fields(p2s_ctx *ctx, int H, int W, int n, const float *d_over_r0,
+                            const unsigned long long *seeds, float *alpha, void *stream) {
+    if (!ctx || (!alpha && n > 0)) return einval("ctx and alpha must be non-NULL");
+    p2s_status st = check_frames_meta(n, d_over_r0, seeds);
+    if (st != P2S_OK) return st;
+    FieldGeom g;
+    if ((st = geometry(ctx, H, W, &g)) != P2S_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+        const int nb = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
+        FrameBatch fb;
+        fill_batch(&fb, nb, d_over_r0 + i0, seeds + i0);
+        void *scratch = nullptr;
+        P2S_CUDA(cudaMallocAsync(&scratch, fields_scratch_bytes(g, nb), s));
+        st = launch_fields(ctx, g, fb, alpha + (size_t)i0 * g.Ah * g.Aw * kAlphaStride, scratch, s);
+        cudaFreeAsync(scratch, s);
+        if (st != P2S_OK) return st;
+    }
+    return P2S_OK;
+}
+
+static p2s_status check_image(const p2s_image *im, const char *what) {
+    if (!im || !im->data) {
+        set_error("%s: NULL image or data", what);
+        return P2S_EINVAL;
+    }
+    if (im->H < 1 || im->W < 1 || !(im->C == 1 || im->C == 3)) {
+        set_error("%s: need H, W >= 1 and C in {1, 3}", what);
+        return P2S_EINVAL;
+    }
+    return P2S_OK;
+}
+
+static bool same_shape(const p2s_image *a, const p2s_image *b) { return a->H == b->H && a->W == b->W && a->C == b->C; }
+
+p2s_status p2s_stage_warp(p2s_ctx *ctx, const p2s_image *in, const float *alpha, const p2s_image *out, void *stream) {
+    if (!ctx || !alpha) return einval("ctx and alpha must be non-NULL");
+    p2s_status st;
+    if ((st = check_image(in, "in")) != P2S_OK || (st = check_image(out, "out")) != P2S_OK) return st;
+    if (!same_shape(in, out)) return einval("in and out shapes differ");
+    if (in->data == out->data) return einval("out must not alias in");
+    FieldGeom g;
+    if ((st = geometry(ctx, in->H, in->W, &g)) != P2S_OK) return st;
+    const float *ip[1] = {in->data};
+    float *op[1] = {out->data};
+    return launch_warp(ctx, g, 1, ip, alpha, op, in->C, (cudaStream_t)stream);
+}
+
+p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *beta, void *stream) {
+    if (!ctx || !alpha || !beta) return einval("ctx, alpha and beta must be non-NULL");
+    FieldGeom g;
+    p2s_status st = geometry(ctx, H, W, &g);
+    if (st != P2S_OK) return st;
+    return launch_mlp_simt(ctx, g, 1, alpha, beta, (cudaStream_t)stream);
+}
+
+p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, const p2s_image *out, void *stream) {
+    if (!ctx || !beta) return einval("ctx and beta must be non-NULL");
+    p2s_status st;
+    if ((st = check_image(xw, "xw")) != P2S_OK || (st = check_image(out, "out")) != P2S_OK) return st;
+    if (!same_shape(xw, out)) return einval("xw and out shapes differ");
+    if (xw->data == out->data) return einval("out must not alias xw");
+    const float *ip[1] = {xw->data};
+    float *op[1] = {out->data};
+    return launch_blur_simt(ctx, xw->H, xw->W, xw->C, 1, ip, beta, op, ctx->form, (cudaStream_t)stream);
+}
+
+// ---- the whole path --------------------------------------------------------
+
+static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2s_image *out, const int *idx, int n,
+                                 const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s) {
+    const int H = frames[idx[0]].H, W = frames[idx[0]].W, C = frames[idx[0]].C;
+    FieldGeom g;
+    p2s_status st = geometry(ctx, H, W, &g);
+    if (st != P2S_OK) return st;
+    const size_t npx = (size_t)H * W;
+    // bound the FP32 path's beta scratch to ~1 GiB per launch group
+    int chunk = kMaxBatch;
+    const size_t beta_px = npx * ctx->K * sizeof(float);
+    while (chunk > 1 && (size_t)chunk * beta_px > (1ull << 30)) chunk /= 2;
+    for (int i0 = 0; i0 < n; i0 += chunk) {
+        const int nb = n - i0 < chunk ? n - i0 : chunk;
+        FrameBatch fb;
+        float dr[kMaxBatch];
+        unsigned long long sd[kMaxBatch];
+        const float *ip[kMaxBatch];
+        float *op[kMaxBatch];
+        for (int i = 0; i < nb; ++i) {
+            const int f = idx[i0 + i];
+            dr[i] = d_over_r0[f];
+            sd[i] = seeds[f];
+            ip[i] = frames[f].data;
+            op[i] = out[f].data;
+        }
+        fill_batch(&fb, nb, dr, sd);
+        const size_t a_bytes = (size_t)nb * g.Ah * g.Aw * kAlphaStride * sizeof(float);
+        const size_t f_bytes = fields_scratch_bytes(g, nb);
+        const size_t xw_bytes = (size_t)nb * npx * C * sizeof(float);
+        const size_t b_bytes = (size_t)nb * beta_px;
+        char *scratch = nullptr;
+        P2S_CUDA(cudaMallocAsync((void **)&scratch, a_bytes + f_bytes + xw_bytes + b_bytes + 1024, s));
+        float *alpha = (float *)scratch;
+        void *fscr = scratch + ((a_bytes + 255) & ~(size_t)255);
+        float *xw = (float *)((char *)fscr + ((f_bytes + 255) & ~(size_t)255));
+        float *beta = (float *)((char *)xw + ((xw_bytes + 255) & ~(size_t)255));
+        const float *xwp[kMaxBatch];
+        float *xwm[kMaxBatch];
+        for (int i = 0; i < nb; ++i) {
+            xwm[i] = xw + (size_t)i * npx * C;
+            xwp[i] = xwm[i];
+        }
+        st = launch_fields(ctx, g, fb, alpha, fscr, s);
+        if (st == P2S_OK) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
+        if (st == P2S_OK) st = launch_mlp_simt(ctx, g, nb, alpha, beta, s);
+        if (st == P2S_OK) st = launch_blur_simt(ctx, H, W, C, nb, xwp, beta, op, ctx->form, s);
+        cudaFreeAsync(scratch, s);
+        if (st != P2S_OK) return st;
+    }
+    return P2S_OK;
+}
+
+static p2s_status validate_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                                    const unsigned long long *seeds, const p2s_image *out) {
+    if (!ctx) return einval("ctx is NULL");
+    p2s_status st = check_frames_meta(n, d_over_r0, seeds);
+    if (st != P2S_OK) return st;
+    if (n > 0 && (!frames || !out)) return einval("frames and out must be non-NULL");
+    for (int i = 0; i < n; ++i) {
+        if ((st = check_image(&frames[i], "frames[i]")) != P2S_OK || (st = check_image(&out[i], "out[i]")) != P2S_OK)
+            return st;
+        if (!same_shape(&frames[i], &out[i])) return einval("frames[i] and out[i] shapes differ");
+        if (frames[i].data == out[i].data) return einval("out[i] must not alias frames[i]");
+        FieldGeom g;
+        if ((st = geometry(ctx, frames[i].H, frames[i].W, &g)) != P2S_OK) return st;
+    }
+    return P2S_OK;
+}
+
+p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                        const unsigned long long *seeds, const p2s_image *out, void *stream) {
+    p2s_status st = validate_simulate(ctx, frames, n, d_over_r0, seeds, out);
+    if (st != P2S_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // group frames of one shape, in order of first appearance
+    std::vector<char> done(n, 0);
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        idx.clear();
+        for (int j = i; j < n; ++j)
+            if (!done[j] && same_shape(&frames[i], &frames[j])) {
+                idx.push_back(j);
+                done[j] = 1;
+            }
+        st = simulate_group(ctx, frames, out, idx.data(), (int)idx.size(), d_over_r0, seeds, s);
+        if (st != P2S_OK) return st;
+    }
+    return P2S_OK;
+}
+
+p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                             const unsigned long long *seeds, const p2s_image *out, void *stream) {
+    p2s_status st = validate_simulate(ctx, frames, n, d_over_r0, seeds, out);
+    if (st != P2S_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) total += 2 * (((size_t)frames[i].H * frames[i].W * frames[i].C * 4 + 255) & ~(size_t)255);
+    char *buf = nullptr;
+    P2S_CUDA(cudaMallocAsync((void **)&buf, total + 256, s));
+    std::vector<p2s_image> din(n), dout(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t bytes = (size_t)frames[i].H * frames[i].W * frames[i].C * 4;
+        din[i] = frames[i];
+        din[i].data = (float *)(buf + off);
+        off += (bytes + 255) & ~(size_t)255;
+        dout[i] = out[i];
+        dout[i].data = (float *)(buf + off);
+        off += (bytes + 255) & ~(size_t)255;
+        if (cudaMemcpyAsync(din[i].data, frames[i].data, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaFreeAsync(buf, s);
+            set_error("host->device copy failed");
+            return P2S_ECUDA;
+        }
+    }
+    st = p2s_simulate(ctx, din.data(), n, d_over_r0, seeds, dout.data(), stream);
+    for (int i = 0; st == P2S_OK && i < n; ++i) {
+        const size_t bytes = (size_t)out[i].H * out[i].W * out[i].C * 4;
+        if (cudaMemcpyAsync(out[i].data, dout[i].data, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            set_error("device->host copy failed");
+            st = P2S_ECUDA;
+        }
+    }
+    cudaFreeAsync(buf, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == P2S_OK) {
+        set_error("stream synchronize failed: %s", cudaGetErrorString(cudaGetLastError()));
+        st = P2S_ECUDA;
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libp2s.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/p2s.h"
+
+namespace p2s {
+
+constexpr int kModes = 35;        // Noll J = 2..36 on the anchor grid
+constexpr int kAlphaStride = 36;  // floats per anchor: slot 0 piston, slot j-1 mode j
+constexpr int kHiModes = 33;      // J = 4..36, the network input
+constexpr int kMaxBatch = 64;     // frames per launch (kernel parameters by value)
+
+void set_error(const char *fmt, ...);
+
+#define P2S_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ::p2s::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                             __FILE__, __LINE__);                                   \
+            return P2S_ECUDA;                                                       \
+        }                                                                           \
+    } while (0)
+
+// Shape of the anchor grid and the filter torus for an H x W frame.
+struct FieldGeom {
+    int H, W, s;
+    int Ah, Aw;  // anchors
+    int Fh, Fw;  // torus (powers of two)
+};
+
+// Per-launch frame parameters, passed by value.
+struct FrameBatch {
+    int n;
+    unsigned long long seed[kMaxBatch];
+    float scale[kMaxBatch];  // (D/r0)^(5/6), computed in FP64 on the host
+};
+
+// Device tables of the separable field filter for one torus length F.
+struct FilterTable {
+    int F = 0;
+    float2 *twiddle = nullptr;  // [F/2]  exp(-2 pi i m / F)
+    float *gain = nullptr;      // [n_kernels][F]  sqrt(C1[u]) / F  (IDFT 1/F folded in)
+};
+
+// Tensor-core operand packs (filled by the tcgen05 translation unit).
+struct TcPack {
+    void *d_W = nullptr;      // packed network weights (canonical smem image)
+    void *d_H = nullptr;      // packed basis chunks (canonical smem image)
+    float *d_bias = nullptr;  // FP32 biases
+    size_t W_bytes = 0, H_bytes = 0;
+    int ready = 0;
+};
+
+}  // namespace p2s
+
+namespace p2s {
+struct ProfRecord {
+    const char *name;
+    cudaEvent_t start, stop;
+    double flops, bytes;
+};
+}  // namespace p2s
+
+struct p2s_ctx {
+    int device = 0;
+    p2s_precision prec = P2S_FP32;
+    p2s_blur_form form = P2S_SCATTER;
+    // basis
+    int K = 0, th = 0, tw = 0, T = 0;
+    std::vector<double> H;  // host FP64 [K][T]
+    float *d_H32 = nullptr; // device FP32 [K][T]
+    float *d_Ht32 = nullptr;// device FP32 [T][K] (tap-major)
+    // network
+    int n_layers = 0;
+    std::vector<int> dims;
+    std::vector<std::vector<double>> W, b;
+    std::vector<float *> d_Wt32;  // FP32 [in][out] per layer
+    std::vector<float *> d_b32;   // FP32 [out] per layer
+    // field correlation
+    int s = 8, n_kernels = 1, guard = 0;
+    std::vector<double> ell;
+    double kappa = 0.0;
+    float *d_L = nullptr;          // FP32 lower Cholesky factor [35][35]
+    int kernel_of_mode[p2s::kModes];
+    int *d_kernel_of_mode = nullptr;
+    std::map<int, p2s::FilterTable> tables;
+    p2s::TcPack tc;
+    // staging for p2s_simulate_host
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    // kernel timing
+    bool profiling = false;
+    std::vector<p2s::ProfRecord> prof;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace p2s {
+
+// Brackets one kernel launch with CUDA events on its stream while the
+// context is profiling; flops/bytes are the launch's algorithmic work.
+class ProfScope {
+  public:
+    ProfScope(const p2s_ctx *ctx, cudaStream_t st, const char *name, double flops, double bytes);
+    ~ProfScope();
+
+  private:
+    p2s_ctx *ctx_;
+    cudaStream_t st_;
+    int idx_ = -1;
+};
+
+// host setup (p2s_host.cu)
+p2s_status geometry(const p2s_ctx *ctx, int H, int W, FieldGeom *g);
+p2s_status filter_table(p2s_ctx *ctx, int F, const FilterTable **out);
+
+// fields (k_fields.cu)
+p2s_status launch_noise(unsigned long long seed, int mode, int Fh, int Fw, float *out, cudaStream_t st);
+size_t fields_scratch_bytes(const FieldGeom &g, int n);
+p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb, float *alpha, void *scratch,
+                         cudaStream_t st);
+
+// warp (k_warp.cu)
+p2s_status launch_warp(const p2s_ctx *ctx, const FieldGeom &g, int n, const float *const *in, const float *alpha,
+                       float *const *out, int C, cudaStream_t st);
+
+// plain FP32 network and blur (k_simt.cu)
+p2s_status launch_mlp_simt(const p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, float *beta,
+                           cudaStream_t st);
+p2s_status launch_blur_simt(const p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw,
+                            const float *beta, float *const *y, p2s_blur_form form, cudaStream_t st);
+
+}  // namespace p2s

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libp2s (include/p2s.h), same names as the C ABI.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors passed by data_ptr on the
+current torch stream.  The library is loaded on first use; a missing library
+raises immediately (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libp2s.so")
+
+P2S_OK, P2S_EINVAL, P2S_ENOMEM, P2S_ECUDA, P2S_ETIMEOUT, P2S_EBUSY, P2S_EUNSUPPORTED = range(7)
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp16": 3}
+FORMS = {"scatter": 0, "gather": 1, "fft": 2}
+
+
+class p2s_basis(C.Structure):
+    _fields_ = [("H", C.POINTER(C.c_double)), ("K", C.c_int), ("taps_h", C.c_int), ("taps_w", C.c_int)]
+
+
+class p2s_mlp(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("dims", C.POINTER(C.c_int)),
+                ("W", C.POINTER(C.POINTER(C.c_double))), ("b", C.POINTER(C.POINTER(C.c_double)))]
+
+
+class p2s_corr_params(C.Structure):
+    _fields_ = [("anchor_spacing", C.c_int), ("n_kernels", C.c_int), ("corr_len_px", C.POINTER(C.c_double)),
+                ("fft_guard", C.c_int), ("kappa", C.c_double)]
+
+
+class p2s_image(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("H", C.c_int), ("W", C.c_int), ("C", C.c_int)]
+
+
+class p2s_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int), ("total_ms", C.c_double), ("flops", C.c_double),
+                ("bytes", C.c_double)]
+
+
+class p2s_geometry(C.Structure):
+    _fields_ = [("anchors_h", C.c_int), ("anchors_w", C.c_int), ("torus_h", C.c_int), ("torus_w", C.c_int),
+                ("alpha_stride", C.c_int)]
+
+
+# every symbol include/p2s.h declares, with its signature
+_SIGS = {
+    "p2s_create": (C.c_int, [C.POINTER(p2s_basis), C.POINTER(p2s_mlp), C.POINTER(p2s_corr_params), C.c_int, C.c_int,
+                             C.POINTER(C.c_void_p)]),
+    "p2s_destroy": (None, [C.c_void_p]),
+    "p2s_status_string": (C.c_char_p, [C.c_int]),
+    "p2s_last_error": (C.c_char_p, []),
+    "p2s_geometry_of": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(p2s_geometry)]),
+    "p2s_simulate": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_int, C.POINTER(C.c_float),
+                               C.POINTER(C.c_ulonglong), C.POINTER(p2s_image), C.c_void_p]),
+    "p2s_simulate_host": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_int, C.POINTER(C.c_float),
+                                    C.POINTER(C.c_ulonglong), C.POINTER(p2s_image), C.c_void_p]),
+    "p2s_stage_noise": (C.c_int, [C.c_void_p, C.c_ulonglong, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "p2s_stage_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_float),
+                                   C.POINTER(C.c_ulonglong), C.c_void_p, C.c_void_p]),
+    "p2s_stage_warp": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
+    "p2s_stage_mlp": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "p2s_stage_blur": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
+    "p2s_noll_covariance": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "p2s_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "p2s_profile_read": (C.c_int, [C.c_void_p, C.POINTER(p2s_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libp2s.so (built in-tree by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libp2s.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class P2SError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = L.p2s_status_string(status).decode()
+        detail = L.p2s_last_error().decode()
+        super().__init__(f"{where}: {msg} ({detail})")
+        self.status = status
+
+
+def _check(st: int, where: str):
+    if st != P2S_OK:
+        raise P2SError(st, where)
+
+
+def noll_covariance(j_max: int = 36) -> np.ndarray:
+    """R_Z for modes 2..j_max at D/r0 = 1, computed by the library (host FP64)."""
+    n = j_max - 1
+    out = np.zeros(n * n, dtype=np.float64)
+    _check(lib().p2s_noll_covariance(j_max, out.ctypes.data_as(C.POINTER(C.c_double))), "p2s_noll_covariance")
+    return out.reshape(n, n)
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _image(t) -> p2s_image:
+    if t.dtype.__str__() != "torch.float32" or not t.is_contiguous():
+        raise ValueError("images must be contiguous float32 tensors [H, W, C]")
+    h, w, c = t.shape
+    return p2s_image(C.c_void_p(t.data_ptr()), h, w, c)
+
+
+def _host_image(a: np.ndarray) -> p2s_image:
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host images must be contiguous float32 arrays [H, W, C]")
+    h, w, c = a.shape
+    return p2s_image(C.c_void_p(a.ctypes.data), h, w, c)
+
+
+class Simulator:
+    """p2s_create / p2s_destroy around a context, plus the per-call entry points."""
+
+    def __init__(self, basis: np.ndarray, taps, layers, anchor_spacing: int = 8, corr_len_px=(16.0,),
+                 fft_guard: int = -1, kappa: float = 0.0, precision: str = "fp32", form: str = "scatter"):
+        L = lib()
+        H = np.ascontiguousarray(basis, dtype=np.float64)
+        self.K, self.T = H.shape
+        self.taps = (int(taps[0]), int(taps[1]))
+        self._keep = [H]
+        b = p2s_basis(H.ctypes.data_as(C.POINTER(C.c_double)), self.K, self.taps[0], self.taps[1])
+        dims = [layers[0][0].shape[1]] + [W.shape[0] for W, _ in layers]
+        dims_a = (C.c_int * len(dims))(*dims)
+        Ws = [np.ascontiguousarray(W, dtype=np.float64) for W, _ in layers]
+        bs = [np.ascontiguousarray(bb, dtype=np.float64) for _, bb in layers]
+        self._keep += Ws + bs
+        Wp = (C.POINTER(C.c_double) * len(Ws))(*[w.ctypes.data_as(C.POINTER(C.c_double)) for w in Ws])
+        bp = (C.POINTER(C.c_double) * len(bs))(*[v.ctypes.data_as(C.POINTER(C.c_double)) for v in bs])
+        m = p2s_mlp(len(layers), dims_a, Wp, bp)
+        ell = np.ascontiguousarray(corr_len_px, dtype=np.float64)
+        self._keep.append(ell)
+        cp = p2s_corr_params(int(anchor_spacing), len(ell), ell.ctypes.data_as(C.POINTER(C.c_double)), int(fft_guard),
+                             float(kappa))
+        ctx = C.c_void_p()
+        _check(L.p2s_create(C.byref(b), C.byref(m), C.byref(cp), PRECISIONS[precision], FORMS[form], C.byref(ctx)),
+               "p2s_create")
+        self.ctx = ctx
+        self.precision, self.form = precision, form
+        self.anchor_spacing = anchor_spacing
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().p2s_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, enable: bool):
+        """Start (clearing) or stop per-kernel event timing."""
+        _check(lib().p2s_profile(self.ctx, 1 if enable else 0), "p2s_profile")
+
+    def profile_read(self) -> list:
+        """[{name, launches, total_ms, flops, bytes}] aggregated per kernel name."""
+        arr = (p2s_kernel_stat * 64)()
+        n = C.c_int()
+        _check(lib().p2s_profile_read(self.ctx, arr, 64, C.byref(n)), "p2s_profile_read")
+        return [dict(name=arr[i].name.decode(), launches=arr[i].launches, total_ms=arr[i].total_ms,
+                     flops=arr[i].flops, bytes=arr[i].bytes) for i in range(min(n.value, 64))]
+
+    def geometry(self, H: int, W: int) -> dict:
+        g = p2s_geometry()
+        _check(lib().p2s_geometry_of(self.ctx, H, W, C.byref(g)), "p2s_geometry_of")
+        return {f: getattr(g, f) for f, _ in p2s_geometry._fields_}
+
+    @staticmethod
+    def _meta(d_over_r0, seeds, n):
+        dr = np.ascontiguousarray(np.broadcast_to(np.asarray(d_over_r0, dtype=np.float32), (n,)))
+        sd = np.ascontiguousarray(np.broadcast_to(np.asarray(seeds, dtype=np.uint64), (n,)))
+        return dr, sd
+
+    def simulate(self, frames, d_over_r0, seeds, out=None, stream=None):
+        """frames: list of CUDA tensors [H, W, C] (or a tensor [n, H, W, C]); returns the outputs."""
+        torch = _torch()
+        frames = list(frames)
+        n = len(frames)
+        if out is None:
+            out = [torch.empty_like(f) for f in frames]
+        dr, sd = self._meta(d_over_r0, seeds, n)
+        fi = (p2s_image * max(n, 1))(*[_image(f) for f in frames])
+        oi = (p2s_image * max(n, 1))(*[_image(o) for o in out])
+        _check(lib().p2s_simulate(self.ctx, fi, n, dr.ctypes.data_as(C.POINTER(C.c_float)),
+                                  sd.ctypes.data_as(C.POINTER(C.c_ulonglong)), oi, _stream_handle(stream)),
+               "p2s_simulate")
+        return out
+
+    def simulate_host(self, frames, d_over_r0, seeds, out=None, stream=None):
+        """Host (NumPy float32) frames in and out; copies happen inside the call."""
+        frames = list(frames)
+        n = len(frames)
+        if out is None:
+            out = [np.empty_like(f) for f in frames]
+        dr, sd = self._meta(d_over_r0, seeds, n)
+        fi = (p2s_image * max(n, 1))(*[_host_image(f) for f in frames])
+        oi = (p2s_image * max(n, 1))(*[_host_image(o) for o in out])
+        _check(lib().p2s_simulate_host(self.ctx, fi, n, dr.ctypes.data_as(C.POINTER(C.c_float)),
+                                       sd.ctypes.data_as(C.POINTER(C.c_ulonglong)), oi, _stream_handle(stream)),
+               "p2s_simulate_host")
+        return out
+
+    def stage_noise(self, seed: int, mode: int, torus_h: int, torus_w: int, stream=None):
+        torch = _torch()
+        out = torch.empty(torus_h * torus_w, dtype=torch.float32, device="cuda")
+        _check(lib().p2s_stage_noise(self.ctx, int(seed), int(mode), torus_h, torus_w, C.c_void_p(out.data_ptr()),
+                                     _stream_handle(stream)), "p2s_stage_noise")
+        return out.view(torus_h, torus_w)
+
+    def stage_fields(self, H: int, W: int, d_over_r0, seeds, stream=None):
+        torch = _torch()
+        n = len(np.atleast_1d(seeds))
+        g = self.geometry(H, W)
+        out = torch.empty((n, g["anchors_h"], g["anchors_w"], g["alpha_stride"]), dtype=torch.float32, device="cuda")
+        dr, sd = self._meta(d_over_r0, seeds, n)
+        _check(lib().p2s_stage_fields(self.ctx, H, W, n, dr.ctypes.data_as(C.POINTER(C.c_float)),
+                                      sd.ctypes.data_as(C.POINTER(C.c_ulonglong)), C.c_void_p(out.data_ptr()),
+                                      _stream_handle(stream)), "p2s_stage_fields")
+        return out
+
+    def stage_warp(self, x, alpha, stream=None):
+        torch = _torch()
+        out = torch.empty_like(x)
+        _check(lib().p2s_stage_warp(self.ctx, C.byref(_image(x)), C.c_void_p(alpha.data_ptr()), C.byref(_image(out)),
+                                    _stream_handle(stream)), "p2s_stage_warp")
+        return out
+
+    def stage_mlp(self, H: int, W: int, alpha, stream=None):
+        torch = _torch()
+        out = torch.empty((H, W, self.K), dtype=torch.float32, device="cuda")
+        _check(lib().p2s_stage_mlp(self.ctx, H, W, C.c_void_p(alpha.data_ptr()), C.c_void_p(out.data_ptr()),
+                                   _stream_handle(stream)), "p2s_stage_mlp")
+        return out
+
+    def stage_blur(self, xw, beta, stream=None):
+        torch = _torch()
+        out = torch.empty_like(xw)
+        if not beta.is_contiguous() or beta.dtype != torch.float32:
+            raise ValueError("beta must be contiguous float32 [H, W, K]")
+        _check(lib().p2s_stage_blur(self.ctx, C.byref(_image(xw)), C.c_void_p(beta.data_ptr()), C.byref(_image(out)),
+                                    _stream_handle(stream)), "p2s_stage_blur")
+        return out
