@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Throughput of the P2S per-frame synthesis path on GB300.
+
+Workload (one step): 64 RGB frames of 512 x 512, K = 100 basis PSFs of 33 x 33
+taps (dictionary of 50,000 PSFs), network 33-128-128-100, D/r0 ~ U[1, 5],
+Philox seed 10^6 + i per frame, synthetic blob images.  A step is one
+p2s_simulate call over the batch: fields, warp, network and blur.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp16|fp32]
+                  [--form scatter|gather] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(test infrastructure) on the host cores on a bounded sample of the same
+workload, the only other place this script runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "P2S frames/s & Mpix/s at 512² RGB K=100 vs roofline; p50/p99 frame latency"
+N_FRAMES, HW, CH, K, TAPS, N_DICT = 64, 512, 3, 100, 33, 50_000
+DIMS = [33, 128, 128, 100]
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def workload_name(precision: str, form: str) -> str:
+    return (f"{N_FRAMES} RGB frames {HW}x{HW}, K={K}, {TAPS}x{TAPS} taps, MLP 33-128-128-100, "
+            f"{precision} {form} blur, D/r0~U[1,5]")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as td
+
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl")
+        return td, rank, world, local
+    return None, rank, world, local
+
+
+def oracle_frame_time(H, layers, x, dr, seed, rows=None):
+    """Seconds the FP64 oracle takes for frame x (or its first `rows` rows)."""
+    import oracle
+
+    if rows is not None:
+        x = x[:rows]
+    t0 = time.perf_counter()
+    oracle.frame.simulate(x.astype(np.float64), seed, dr, H, layers, oracle.fields.CorrParams(8, (16.0,)),
+                          (TAPS, TAPS))
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, bounded sample per step."""
+    _, rank, world, _ = (None, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
+    if rank != 0:
+        return 0
+    from paper_2107_11627_gb300 import basis, inputs
+
+    H = basis.build_basis(K, TAPS, N_DICT)
+    layers = inputs.mlp_weights(DIMS, 42)
+    dr = inputs.frame_strengths(N_FRAMES, 1.0, 5.0, 7)
+    rows = args.ref_rows
+    xs = [inputs.blob_image(HW, HW, CH, 1000 + i) for i in range(args.warmup + args.steps)]
+    for i in range(args.warmup):
+        oracle_frame_time(H, layers, xs[i], float(dr[i % N_FRAMES]), 10**6 + i, rows)
+    ts = [oracle_frame_time(H, layers, xs[args.warmup + i], float(dr[(args.warmup + i) % N_FRAMES]),
+                            10**6 + args.warmup + i, rows) for i in range(args.steps)]
+    frac = rows / HW
+    fps = args.steps * frac / sum(ts)
+    cores = os.cpu_count()
+    sample = f"rows 0..{rows - 1} of one {HW}x{HW}x3 frame per step (full path, FP64 NumPy), scaled to frames"
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.precision, args.form)},
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    global N_FRAMES
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp16", "fp32", "fp8"])
+    ap.add_argument("--form", default="scatter", choices=["scatter", "gather", "fft"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=128, help="rows per step of the reference arm's sample")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=64, help="frames per step (profiling runs only)")
+    args = ap.parse_args()
+    N_FRAMES = args.frames
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2107_11627_gb300 import basis, inputs, p2s
+
+    td, rank, world, local = dist()
+    torch.cuda.set_device(local)
+    Hb = basis.build_basis(K, TAPS, N_DICT)
+    layers = inputs.mlp_weights(DIMS, 42)
+    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,),
+                        precision=args.precision, form=args.form)
+    xs_host = inputs.blob_batch(N_FRAMES, HW, HW, CH, 1000 + rank * N_FRAMES)
+    dr = inputs.frame_strengths(N_FRAMES, 1.0, 5.0, 7 + rank)
+    seeds = inputs.frame_seeds(N_FRAMES, 10**6 + rank * N_FRAMES)
+    xs = [torch.from_numpy(x).cuda() for x in xs_host]
+    ys = [torch.empty_like(x) for x in xs]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sim.simulate(xs, dr, seeds, out=ys)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if td is not None:
+            td.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    sim.profile(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    clocks.start()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    sim.profile(False)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    kstats = sim.profile_read()
+    if td is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        total_ms = float(t.item())
+    frames_total = N_FRAMES * args.steps * world
+    fps = frames_total / (total_ms / 1e3)
+    mpix = fps * HW * HW / 1e6
+
+    # roofline of the dominant kernel, from its own launches in the timed region
+    peaks, peak_src = load_peaks()
+    dom = max(kstats, key=lambda s: s["total_ms"]) if kstats else None
+    roof = None
+    if dom is not None:
+        avg_s = dom["total_ms"] / 1e3 / dom["launches"]
+        if "fp32" in dom["name"]:
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            achieved = dom["flops"] / dom["launches"] / avg_s / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": dom["name"],
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+        elif dom["flops"] > 0:
+            peak = peaks["bf16_tflops_sustained"]
+            achieved = dom["flops"] / dom["launches"] / avg_s / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": dom["name"],
+                    "peak_source": f"{peak_src} bf16_tflops_sustained"}
+        else:
+            peak = peaks["hbm_gbs"]
+            achieved = dom["bytes"] / dom["launches"] / avg_s / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": dom["name"], "peak_source": f"{peak_src} hbm_gbs"}
+    launches = sum(s["launches"] for s in kstats)
+
+    # end to end through the host-buffer entry point: H2D + path + D2H inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        pin_in = [torch.from_numpy(x).pin_memory() for x in xs_host]
+        pin_out = [torch.empty_like(p).pin_memory() for p in pin_in]
+        hin = [p.numpy() for p in pin_in]
+        hout = [p.numpy() for p in pin_out]
+        sim.simulate_host(hin, dr, seeds, out=hout)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.simulate_host(hin, dr, seeds, out=hout)
+        el = time.perf_counter() - t0
+        if td is not None:
+            t = torch.tensor([el], device="cuda")
+            td.all_reduce(t, op=td.ReduceOp.MAX)
+            el = float(t.item())
+        bytes_step = N_FRAMES * HW * HW * CH * 4
+        e2e = {"value": N_FRAMES * args.e2e_steps * world / el, "unit": "frames/s",
+               "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = oracle_frame_time(Hb, layers, xs_host[0], float(dr[0]), int(seeds[0]))
+        cpu = {"value": 1.0 / t, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"frame 0 of the batch ({HW}x{HW}x3), full path, FP64 NumPy, one run"}
+
+    if rank == 0:
+        dtype = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision]
+        line = {"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": {"workload": workload_name(args.precision, args.form), "frames": N_FRAMES, "H": HW,
+                           "W": HW, "C": CH, "K": K, "taps": f"{TAPS}x{TAPS}", "precision": args.precision,
+                           "form": args.form, "anchor_spacing": 8, "parallelism": f"replicas x{world}",
+                           "l2": f"inputs larger than L2 ({N_FRAMES * HW * HW * CH * 4 / 1e6:.0f} MB per step)"},
+                "mpix_per_s": mpix,
+                "latency_ms": {"step_p50": float(np.percentile(step_ms, 50)),
+                               "step_p99": float(np.percentile(step_ms, 99)),
+                               "frame_p50": float(np.percentile(step_ms, 50)) / N_FRAMES},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in kstats]}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if td is not None:
+        td.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

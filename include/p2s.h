@@ -177,6 +177,13 @@ p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *
 p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, const p2s_image *out,
                           void *stream);
 
+/* Synchronises `stream`, then reads and clears the context's device status
+ * word, which a kernel sets when one of its bounded waits gives up (a
+ * pipeline stage stalled for about two seconds).  Returns P2S_ETIMEOUT if it
+ * was set (the outputs of the calls since the last check are then invalid),
+ * P2S_ECUDA if the stream reports an error, P2S_OK otherwise. */
+p2s_status p2s_check(p2s_ctx *ctx, void *stream);
+
 /* ---- kernel timing ------------------------------------------------------- */
 
 /* Per-kernel totals recorded while profiling is on: CUDA events bracket every

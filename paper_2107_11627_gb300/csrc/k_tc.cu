@@ -1,0 +1,737 @@
+// Tensor-core path (tcgen05, sm_103a): the P2S network (Sec. 3.3) and the
+// basis blur (Sec. 3.1, Eq. 5) fused in one persistent kernel.
+//
+// Work unit: a tile of 128 output columns x 32 output rows of one frame,
+// processed two rows at a time.  Per row pair:
+//   network   three tcgen05.mma layers per row (M = 128 pixels), activations
+//             kept in tensor memory between layers (A operand from TMEM);
+//   beta      written into TMEM as the A operand of the contraction, with
+//             two extra "one" columns that pick up the last layer's bias,
+//             folded into the basis as an exact hi/lo pair of rows;
+//   G = beta H  chunk by chunk into TMEM (N = 96: 3 tap columns x 32 tap
+//             rows; the last tap row as a final N = 48 chunk);
+//   gather    y_c[q] += G[q, t] x_c[q - o(t)] on the CUDA cores: each thread
+//             owns one output column of the row pair, walks a tap column with
+//             a 33-row window of x in registers (x staged as FP32 in shared
+//             memory), accumulates in FP32.
+// Roles: warp 0 issues MMAs (one thread), warp 1 streams weights and basis
+// chunks into a 3-slot shared-memory ring with 1-D bulk copies, warps 2..9
+// (two per TMEM lane quadrant) convert between layers and run the gather;
+// the two halves take alternate chunks, each with its own TMEM buffer.
+// Every wait is bounded; a timeout sets the status word and the kernel
+// drains and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "p2s_internal.h"
+#include "tc_ptx.cuh"
+
+namespace p2s {
+namespace tc {
+
+constexpr int kStrip = 128;                    // output columns per tile (TMEM lanes)
+constexpr int kBand = 32;                      // output rows per tile
+constexpr int kHalo = 16;                      // 33 x 33 taps
+constexpr int kTaps = 2 * kHalo + 1;
+constexpr int kTR = kBand + 2 * kHalo;         // x tile rows
+constexpr int kTC = kStrip + 2 * kHalo;        // x tile columns
+constexpr int kKP = 112;                       // padded contraction depth
+constexpr int kKSteps = kKP / 16;
+constexpr int kMainN = 96;                     // main chunk width
+constexpr int kMainChunks = 11;                // 33 tap columns / 3
+constexpr int kChunks = kMainChunks + 1;       // + the last tap row
+constexpr int kLastN = 48;
+constexpr int kSlot = 32768;
+constexpr int kSlots = 3;
+constexpr int kThreads = 320;
+constexpr int kEpi = 256;
+
+// tensor-memory column map (512 columns allocated)
+__host__ __device__ constexpr uint32_t colA1(int r) { return r ? 24u : 0u; }
+__host__ __device__ constexpr uint32_t colD1(int r) { return r ? 256u : 128u; }  // A2 in place
+__host__ __device__ constexpr uint32_t colD2(int r) { return r ? 0u : 384u; }    // A3 in place
+__host__ __device__ constexpr uint32_t colD3(int r) { return r ? 256u : 128u; }
+__host__ __device__ constexpr uint32_t colBeta(int r) { return r ? 56u : 0u; }
+__host__ __device__ constexpr uint32_t colDB(int h) { return h ? 320u : 128u; }  // contraction, 2 rows x 96
+
+enum Mode { kFull = 0, kMlpOnly = 1, kBlurOnly = 2 };
+
+struct Item {
+    uint32_t offset, bytes, n, k;
+};
+
+struct Params {
+    const float *xw[kMaxBatch];
+    float *y[kMaxBatch];
+    const float *alpha;
+    const float *beta_in;
+    float *beta_out;
+    const uint8_t *stream;
+    const float *bias;  // b1 [h1p], b2 [h2p]
+    const float *b3;    // [K]
+    int *status;
+    int n, H, W, C, s, Ah, Aw;
+    float inv_s;
+    int K, h1p, h2p, n3;
+    int mode, fold, ab_fmt, split;
+    int tiles_x, tiles_y, tiles_total;
+    int n_mlp_items;
+    Item item[6 + kChunks];  // network items (hi[,lo] per layer), then chunks
+};
+
+// shared-memory layout
+constexpr int kOffRing = 0;
+constexpr int kOffXrg = kOffRing + kSlots * kSlot;             // float2 [kTR][kTC]
+constexpr int kOffXb = kOffXrg + kTR * kTC * 8;                // float  [kTR][kTC]
+constexpr int kOffBias = kOffXb + kTR * kTC * 4;               // 256 floats
+constexpr int kOffXchg = kOffBias + 256 * 4;                   // [128][6] floats
+constexpr int kOffBar = kOffXchg + kStrip * 6 * 4;             // mbarriers
+// ring full/empty, network stage handshakes, contraction buffer full/empty
+enum Bar { kFull0 = 0, kEmpty0 = 3, kA1b = 6, kD1b, kA2b, kD2b, kA3b, kD3b, kBetab, kDFull0 = 13, kDEmpty0 = 15, kNBar = 17 };
+constexpr int kOffMisc = kOffBar + kNBar * 8;                  // tmem base, abort flag
+constexpr int kSmemBytes = kOffMisc + 16 + 1024;               // + alignment slack
+static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+
+__device__ __forceinline__ uint32_t pack2(float a, float b, int fmt) {
+    if (fmt == 1) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+struct Ctl {
+    volatile int *abort;
+    int *status;
+};
+
+// Bounded wait (about 2 s at 2 GHz); on timeout flags the CTA and the status
+// word.  Once the CTA is flagged every wait returns false at once, so all
+// roles run their (data-independent) loops to the end and meet at teardown.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Ctl &ctl, int code) {
+    if (ptx::mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (ptx::mbar_try(bar, parity)) return true;
+        if (*ctl.abort) return false;
+        if (clock64() - t0 > 4000000000ll) {
+            *ctl.abort = 1;
+            atomicOr(ctl.status, code);
+            return false;
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag: used to let issued bulk copies
+// land before the CTA's shared memory is released.
+__device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!ptx::mbar_try(bar, parity) && clock64() - t0 < 4000000000ll) {
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constant__ Params p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = ptx::smem_u32(sm);
+    float2 *xrg = (float2 *)(sm + kOffXrg);
+    float *xb = (float *)(sm + kOffXb);
+    float *sbias = (float *)(sm + kOffBias);
+    float *xchg = (float *)(sm + kOffXchg);
+    const uint32_t bar0 = sbase + kOffBar;
+    uint32_t *tmem_holder = (uint32_t *)(sm + kOffMisc);
+    volatile int *abort_flag = (volatile int *)(sm + kOffMisc + 4);
+    auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Ctl ctl{abort_flag, p.status};
+
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        for (int i = 0; i < kSlots; ++i) {
+            ptx::mbar_init(BAR(kFull0 + i), 1);
+            ptx::mbar_init(BAR(kEmpty0 + i), 1);
+        }
+        ptx::mbar_init(BAR(kA1b), 8);
+        ptx::mbar_init(BAR(kD1b), 1);
+        ptx::mbar_init(BAR(kA2b), 8);
+        ptx::mbar_init(BAR(kD2b), 1);
+        ptx::mbar_init(BAR(kA3b), 8);
+        ptx::mbar_init(BAR(kD3b), 1);
+        ptx::mbar_init(BAR(kBetab), 8);
+        ptx::mbar_init(BAR(kDFull0), 1);
+        ptx::mbar_init(BAR(kDFull0 + 1), 1);
+        ptx::mbar_init(BAR(kDEmpty0), 4);
+        ptx::mbar_init(BAR(kDEmpty0 + 1), 4);
+        ptx::mbar_fence_init();
+    }
+    for (int i = threadIdx.x; i < p.h1p + p.h2p; i += blockDim.x) sbias[i] = p.bias[i];
+    if (warp == 0) ptx::tmem_alloc(ptx::smem_u32(tmem_holder), 512);
+    ptx::fence_before();
+    __syncthreads();
+    ptx::fence_after();
+    const uint32_t tmem = *tmem_holder;
+    const uint32_t idesc_n96 = ptx::idesc_f16(p.ab_fmt, kMainN);
+    const uint32_t idesc_n48 = ptx::idesc_f16(p.ab_fmt, kLastN);
+    const bool do_mlp = p.mode != kBlurOnly, do_blur = p.mode != kMlpOnly;
+    const int items_per_pair = (do_mlp ? p.n_mlp_items : 0) + (do_blur ? kChunks : 0);
+
+    auto n_pairs_of = [&](int tile) {
+        const int ty = (tile % (p.tiles_x * p.tiles_y)) / p.tiles_x;
+        const int rows = min(kBand, p.H - ty * kBand);
+        return (rows + 1) >> 1;
+    };
+
+    if (warp == 1) {
+        // ---------------- producer: weights and basis chunks into the ring ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
+                const int npair = n_pairs_of(tile);
+                for (int rp = 0; rp < npair; ++rp) {
+                    for (int j = 0; j < items_per_pair; ++j) {
+                        const int id = (do_mlp && j < p.n_mlp_items) ? j : 6 + (j - (do_mlp ? p.n_mlp_items : 0));
+                        const Item itm = p.item[id];
+                        const uint32_t slot = it % kSlots;
+                        if (!wait_bar(BAR(kEmpty0 + slot), ((it / kSlots) & 1) ^ 1, ctl, 1)) continue;
+                        ptx::mbar_arrive_tx(BAR(kFull0 + slot), itm.bytes);
+                        ptx::bulk_g2s(sbase + kOffRing + slot * kSlot, p.stream + itm.offset, itm.bytes,
+                                      BAR(kFull0 + slot));
+                        ++it;
+                    }
+                }
+            }
+            // every issued copy must land before the CTA's shared memory is released
+            for (uint32_t k = (it > (uint32_t)kSlots ? it - kSlots : 0); k < it; ++k)
+                drain_bar(BAR(kFull0 + k % kSlots), (k / kSlots) & 1);
+        }
+    } else if (warp == 0) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t it = 0, pairs = 0, uses[2] = {0, 0};
+            // next ring item: wait until it has landed; returns its shared address (0 if aborted)
+            auto take = [&](uint32_t &slot) -> uint32_t {
+                slot = it % kSlots;
+                const bool ok = wait_bar(BAR(kFull0 + slot), (it / kSlots) & 1, ctl, 2);
+                ++it;
+                return ok ? sbase + kOffRing + slot * kSlot : 0u;
+            };
+            const int per = p.split ? 2 : 1;
+            for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
+                const int npair = n_pairs_of(tile);
+                for (int rp = 0; rp < npair; ++rp, ++pairs) {
+                    const uint32_t ph = pairs & 1;
+                    if (do_mlp) {
+                        const uint32_t a_reg[3][2] = {{colA1(0), colA1(1)}, {colD1(0), colD1(1)}, {colD2(0), colD2(1)}};
+                        const uint32_t d_reg[3][2] = {{colD1(0), colD1(1)}, {colD2(0), colD2(1)}, {colD3(0), colD3(1)}};
+                        const int ready[3] = {kA1b, kA2b, kA3b};
+                        const int done[3] = {kD1b, kD2b, kD3b};
+                        for (int L = 0; L < 3; ++L) {
+                            const bool rdy = wait_bar(BAR(ready[L]), ph, ctl, 4);
+                            ptx::fence_after();
+                            for (int w = 0; w < per; ++w) {
+                                const Item itm = p.item[L * per + w];
+                                uint32_t slot;
+                                const uint32_t sa = take(slot);
+                                if (rdy && sa) {
+                                    ptx::fence_after();
+                                    const uint32_t idesc = ptx::idesc_f16(p.ab_fmt, (int)itm.n);
+                                    const int ksteps = (int)itm.k / 16;
+                                    for (int r = 0; r < 2; ++r)
+                                        for (int ks = 0; ks < ksteps; ++ks) {
+                                            const uint64_t bd = ptx::smem_desc(sa + ks * 2 * (itm.n * 16), itm.n * 16, 128);
+                                            ptx::mma_ts(tmem + d_reg[L][r], tmem + a_reg[L][r] + ks * 8, bd, idesc,
+                                                        (w > 0 || ks > 0) ? 1u : 0u);
+                                        }
+                                }
+                                ptx::mma_commit(BAR(kEmpty0 + slot));
+                            }
+                            ptx::mma_commit(BAR(done[L]));
+                        }
+                    }
+                    const bool brdy = wait_bar(BAR(kBetab), ph, ctl, 8);
+                    ptx::fence_after();
+                    if (do_blur) {
+                        for (int c = 0; c < kChunks; ++c) {
+                            const int h = c & 1;
+                            uint32_t slot;
+                            const uint32_t sa = take(slot);
+                            const bool free_buf = wait_bar(BAR(kDEmpty0 + h), (uses[h] & 1) ^ 1, ctl, 16);
+                            ptx::fence_after();
+                            if (brdy && sa && free_buf) {
+                                const uint32_t n = p.item[6 + c].n;
+                                const uint32_t idesc = (n == (uint32_t)kMainN) ? idesc_n96 : idesc_n48;
+                                for (int r = 0; r < 2; ++r)
+                                    for (int ks = 0; ks < kKSteps; ++ks) {
+                                        const uint64_t bd = ptx::smem_desc(sa + ks * 2 * (n * 16), n * 16, 128);
+                                        ptx::mma_ts(tmem + colDB(h) + r * kMainN, tmem + colBeta(r) + ks * 8, bd, idesc,
+                                                    ks > 0 ? 1u : 0u);
+                                    }
+                            }
+                            ptx::mma_commit(BAR(kEmpty0 + slot));
+                            ptx::mma_commit(BAR(kDFull0 + h));
+                            ++uses[h];
+                        }
+                    }
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: 8 warps, two per TMEM lane quadrant ----------------
+        const int e = warp - 2;
+        const int half = e >> 2;               // 0: warps 2-5, 1: warps 6-9
+        const int quad = warp & 3;             // TMEM lane quadrant of this warp
+        const int col = quad * 32 + lane;      // output column within the strip
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        const int tid_e = threadIdx.x - 64;    // 0..255
+        uint32_t pairs = 0, uses = 0;
+        for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
+            const int per_frame = p.tiles_x * p.tiles_y;
+            const int frame = tile / per_frame;
+            const int ty = (tile % per_frame) / p.tiles_x, tx = tile % p.tiles_x;
+            const int r_band = ty * kBand, c0 = tx * kStrip;
+            const int npair = n_pairs_of(tile);
+            if (do_blur) {
+                ptx::named_bar(1, kEpi);  // previous tile fully consumed
+                const float *x = p.xw[frame];
+                for (int i = tid_e; i < kTR * kTC; i += kEpi) {
+                    const int tr = i / kTC, tcol = i - tr * kTC;
+                    const int gr = r_band - kHalo + tr, gc = c0 - kHalo + tcol;
+                    float r = 0.f, g = 0.f, b = 0.f;
+                    if (gr >= 0 && gr < p.H && gc >= 0 && gc < p.W) {
+                        const float *px = x + ((size_t)gr * p.W + gc) * C;
+                        r = __ldg(px);
+                        if (C == 3) {
+                            g = __ldg(px + 1);
+                            b = __ldg(px + 2);
+                        }
+                    }
+                    xrg[i] = make_float2(r, g);
+                    xb[i] = b;
+                }
+                ptx::named_bar(1, kEpi);
+            }
+            for (int rp = 0; rp < npair; ++rp, ++pairs) {
+                const uint32_t ph = pairs & 1;
+                bool ok = true;
+                const int row = r_band + 2 * rp + half;  // this half's row for network stages
+                const bool col_ok = c0 + col < p.W, row_ok = row < p.H;
+                if (do_mlp) {
+                    // ---- network input: alpha_4..36 at (row, col), bilinear from the anchors ----
+                    {
+                        const int gi = min(row, p.H - 1), gj = min(c0 + col, p.W - 1);
+                        const int ay = gi / p.s, ax = gj / p.s;
+                        const float fy = (float)(gi - ay * p.s) * p.inv_s, fx = (float)(gj - ax * p.s) * p.inv_s;
+                        const float *a = p.alpha + ((size_t)frame * p.Ah * p.Aw + (size_t)ay * p.Aw + ax) * kAlphaStride;
+                        const float *b = a + (size_t)p.Aw * kAlphaStride;
+                        float v[48];
+#pragma unroll
+                        for (int m = 0; m < 48; ++m) {
+                            if (m < kHiModes) {
+                                const int sl = m + 3;
+                                v[m] = (1.0f - fy) * ((1.0f - fx) * __ldg(a + sl) + fx * __ldg(a + kAlphaStride + sl)) +
+                                       fy * ((1.0f - fx) * __ldg(b + sl) + fx * __ldg(b + kAlphaStride + sl));
+                            } else {
+                                v[m] = 0.f;
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            uint32_t u[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) u[j] = pack2(v[16 * q + 2 * j], v[16 * q + 2 * j + 1], p.ab_fmt);
+                            ptx::tmem_st8(lane_base + colA1(half) + 8 * q, u);
+                        }
+                        ptx::tmem_wait_st();
+                        ptx::fence_before();
+                        __syncwarp();
+                        if (lane == 0) ptx::mbar_arrive(BAR(kA1b));
+                    }
+                    // ---- layers 1, 2: D -> bias, ReLU -> packed activations in place ----
+                    const int done[2] = {kD1b, kD2b};
+                    const int ready[2] = {kA2b, kA3b};
+                    const uint32_t dreg[2] = {colD1(half), colD2(half)};
+                    const int width[2] = {p.h1p, p.h2p};
+                    const int boff[2] = {0, p.h1p};
+                    for (int L = 0; L < 2; ++L) {
+                        ok = __all_sync(0xffffffffu, wait_bar(BAR(done[L]), ph, ctl, 32) && ok);
+                        ptx::fence_after();
+                        for (int q = 0; ok && q < width[L] / 32; ++q) {
+                            uint32_t d[32];
+                            ptx::tmem_ld32(lane_base + dreg[L] + 32 * q, d);
+                            ptx::tmem_wait_ld();
+                            uint32_t u[16];
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const float h0 = fmaxf(__uint_as_float(d[2 * j]) + sbias[boff[L] + 32 * q + 2 * j], 0.f);
+                                const float h1 = fmaxf(__uint_as_float(d[2 * j + 1]) + sbias[boff[L] + 32 * q + 2 * j + 1], 0.f);
+                                u[j] = pack2(h0, h1, p.ab_fmt);
+                            }
+                            const uint32_t (&u0)[8] = *reinterpret_cast<const uint32_t(*)[8]>(&u[0]);
+                            const uint32_t (&u1)[8] = *reinterpret_cast<const uint32_t(*)[8]>(&u[8]);
+                            ptx::tmem_st8(lane_base + dreg[L] + 16 * q, u0);
+                            ptx::tmem_st8(lane_base + dreg[L] + 16 * q + 8, u1);
+                        }
+                        ptx::tmem_wait_st();
+                        ptx::fence_before();
+                        __syncwarp();
+                        if (lane == 0) ptx::mbar_arrive(BAR(ready[L]));
+                    }
+                    // ---- layer 3: beta = D3 (+ b3 folded into the basis) ----
+                    ok = __all_sync(0xffffffffu, wait_bar(BAR(kD3b), ph, ctl, 64) && ok);
+                    ptx::fence_after();
+                    if (ok) {
+                        float v[kKP];
+#pragma unroll
+                        for (int q = 0; q < kKP / 16; ++q) {
+                            uint32_t d[16];
+                            if (16 * q < p.n3) {
+                                ptx::tmem_ld16(lane_base + colD3(half) + 16 * q, d);
+                                ptx::tmem_wait_ld();
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) d[j] = 0u;
+                            }
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) v[16 * q + j] = __uint_as_float(d[j]);
+                        }
+                        if (p.mode == kMlpOnly) {
+                            if (row_ok && col_ok) {
+                                float *o = p.beta_out + (((size_t)frame * p.H + row) * p.W + c0 + col) * p.K;
+#pragma unroll
+                                for (int k = 0; k < kKP; ++k)
+                                    if (k < p.K) o[k] = v[k] + __ldg(p.b3 + k);
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < kKP; ++k)
+                                if (k >= p.K) v[k] = (p.fold && (k == p.K || k == p.K + 1)) ? 1.0f : 0.0f;
+#pragma unroll
+                            for (int q = 0; q < kKP / 16; ++q) {
+                                uint32_t u[8];
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) u[j] = pack2(v[16 * q + 2 * j], v[16 * q + 2 * j + 1], p.ab_fmt);
+                                ptx::tmem_st8(lane_base + colBeta(half) + 8 * q, u);
+                            }
+                            ptx::tmem_wait_st();
+                        }
+                    }
+                    ptx::fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(BAR(kBetab));
+                } else {
+                    // blur alone: beta of (row, col) from global, no bias fold
+                    const int gi = min(row, p.H - 1), gj = min(c0 + col, p.W - 1);
+                    const float *bp = p.beta_in + (((size_t)frame * p.H + gi) * p.W + gj) * p.K;
+                    for (int q = 0; q < kKP / 16; ++q) {
+                        uint32_t u[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int k0 = 16 * q + 2 * j;
+                            const float a0 = k0 < p.K ? __ldg(bp + k0) : 0.f;
+                            const float a1 = k0 + 1 < p.K ? __ldg(bp + k0 + 1) : 0.f;
+                            u[j] = pack2(a0, a1, p.ab_fmt);
+                        }
+                        ptx::tmem_st8(lane_base + colBeta(half) + 8 * q, u);
+                    }
+                    ptx::tmem_wait_st();
+                    ptx::fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(BAR(kBetab));
+                }
+                if (!do_blur) continue;
+                // ---- contraction chunks: this half takes chunks c with c % 2 == half ----
+                float acc[2][3];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) acc[i][ch] = 0.f;
+                const uint32_t buf = lane_base + colDB(half);
+                for (int c = half; c < kChunks; c += 2) {
+                    const bool got = __all_sync(0xffffffffu, wait_bar(BAR(kDFull0 + half), uses & 1, ctl, 128));
+                    ok = ok && got;
+                    ptx::fence_after();
+                    if (!got) {
+                    } else if (c < kMainChunks) {
+#pragma unroll 1
+                        for (int u3 = 0; u3 < 3; ++u3) {
+                            const int txx = 3 * c + u3;  // tap column 0..32
+                            uint32_t g0[32], g1[32];
+                            ptx::tmem_ld32(buf + 32 * u3, g0);
+                            ptx::tmem_ld32(buf + kMainN + 32 * u3, g1);
+                            float wr[33], wg[33], wb[33];
+                            const int base = (2 * rp + 1) * kTC + col + 32 - txx;
+#pragma unroll
+                            for (int j = 0; j < 33; ++j) {
+                                const float2 rg = xrg[base + j * kTC];
+                                wr[j] = rg.x;
+                                wg[j] = rg.y;
+                                wb[j] = (C == 3) ? xb[base + j * kTC] : 0.f;
+                            }
+                            ptx::tmem_wait_ld();
+#pragma unroll
+                            for (int t = 0; t < 32; ++t) {
+                                const float a = __uint_as_float(g0[t]), b = __uint_as_float(g1[t]);
+                                acc[0][0] = fmaf(a, wr[31 - t], acc[0][0]);
+                                acc[1][0] = fmaf(b, wr[32 - t], acc[1][0]);
+                                if (C == 3) {
+                                    acc[0][1] = fmaf(a, wg[31 - t], acc[0][1]);
+                                    acc[0][2] = fmaf(a, wb[31 - t], acc[0][2]);
+                                    acc[1][1] = fmaf(b, wg[32 - t], acc[1][1]);
+                                    acc[1][2] = fmaf(b, wb[32 - t], acc[1][2]);
+                                }
+                            }
+                        }
+                    } else {
+                        // last tap row (dy = +16): 33 tap columns, source rows 2rp + i of the tile
+                        uint32_t g0[48], g1[48];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            ptx::tmem_ld16(buf + 16 * q, *reinterpret_cast<uint32_t(*)[16]>(&g0[16 * q]));
+                            ptx::tmem_ld16(buf + kMainN + 16 * q, *reinterpret_cast<uint32_t(*)[16]>(&g1[16 * q]));
+                        }
+                        ptx::tmem_wait_ld();
+#pragma unroll
+                        for (int txx = 0; txx < kTaps; ++txx) {
+                            const int i0 = (2 * rp) * kTC + col + 32 - txx, i1 = i0 + kTC;
+                            const float a = __uint_as_float(g0[txx]), b = __uint_as_float(g1[txx]);
+                            const float2 rg0 = xrg[i0], rg1 = xrg[i1];
+                            acc[0][0] = fmaf(a, rg0.x, acc[0][0]);
+                            acc[1][0] = fmaf(b, rg1.x, acc[1][0]);
+                            if (C == 3) {
+                                acc[0][1] = fmaf(a, rg0.y, acc[0][1]);
+                                acc[0][2] = fmaf(a, xb[i0], acc[0][2]);
+                                acc[1][1] = fmaf(b, rg1.y, acc[1][1]);
+                                acc[1][2] = fmaf(b, xb[i1], acc[1][2]);
+                            }
+                        }
+                    }
+                    ptx::fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(BAR(kDEmpty0 + half));
+                    ++uses;
+                }
+                // ---- combine the halves, write the row pair ----
+                if (half == 1) {
+#pragma unroll
+                    for (int i = 0; i < 2; ++i)
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) xchg[col * 6 + i * 3 + ch] = acc[i][ch];
+                }
+                ptx::named_bar(2, kEpi);
+                if (half == 0 && ok) {
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int orow = r_band + 2 * rp + i;
+                        if (orow < p.H && col_ok) {
+                            float *o = p.y[frame] + ((size_t)orow * p.W + c0 + col) * C;
+#pragma unroll
+                            for (int ch = 0; ch < C; ++ch) o[ch] = acc[i][ch] + xchg[col * 6 + i * 3 + ch];
+                        }
+                    }
+                }
+                ptx::named_bar(2, kEpi);
+            }
+        }
+    }
+    // ---------------- teardown ----------------
+    ptx::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        ptx::fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
+__host__ inline uint16_t to_half_bits(double v, int fmt) {
+    if (fmt == 1) {
+        __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        uint16_t u;
+        std::memcpy(&u, &h, 2);
+        return u;
+    }
+    __half h = __float2half_rn((float)v);
+    uint16_t u;
+    std::memcpy(&u, &h, 2);
+    return u;
+}
+__host__ inline double from_half_bits(uint16_t u, int fmt) {
+    if (fmt == 1) {
+        __nv_bfloat16 h;
+        std::memcpy(&h, &u, 2);
+        return (double)__bfloat162float(h);
+    }
+    __half h;
+    std::memcpy(&h, &u, 2);
+    return (double)__half2float(h);
+}
+
+// canonical K-major, no swizzle: (n, k) -> byte offset; rows N (multiple of 8)
+__host__ inline size_t canon(int n, int k, int N) { return (size_t)(k / 8) * (N * 16) + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2; }
+
+}  // namespace tc
+
+using namespace tc;
+
+static int round16(int v) { return (v + 15) & ~15; }
+static int round32(int v) { return (v + 31) & ~31; }
+
+// Pack the network weights and the basis chunks into one stream of B images.
+p2s_status tc_prepare(p2s_ctx *ctx) {
+    if (ctx->tc.ready) return P2S_OK;
+    const int fmt = ctx->prec == P2S_BF16 ? 1 : 0;
+    const int split = ctx->prec == P2S_BF16 ? 1 : 0;
+    if (ctx->n_layers != 3 || ctx->th != kTaps || ctx->tw != kTaps || ctx->K > kKP - 2 || ctx->dims[1] > 128 ||
+        ctx->dims[2] > 128) {
+        set_error("tensor-core path needs 3 layers (widths <= 128), 33x33 taps and K <= %d", kKP - 2);
+        return P2S_EUNSUPPORTED;
+    }
+    const int K = ctx->K, T = ctx->T;
+    const int h1p = round32(ctx->dims[1]), h2p = round32(ctx->dims[2]), n3 = round16(K);
+    std::vector<uint8_t> buf;
+    std::vector<Item> items;
+    auto add_image = [&](int N, int Kd, auto value) {
+        Item it{(uint32_t)buf.size(), (uint32_t)(N * Kd * 2), (uint32_t)N, (uint32_t)Kd};
+        buf.resize(buf.size() + it.bytes, 0);
+        uint8_t *base = buf.data() + it.offset;
+        for (int n = 0; n < N; ++n)
+            for (int k = 0; k < Kd; ++k) {
+                const uint16_t u = value(n, k);
+                std::memcpy(base + canon(n, k, N), &u, 2);
+            }
+        items.push_back(it);
+    };
+    // network: layer l weights W[l] [out][in] as B = [N = out][K = in]
+    const int ins[3] = {kHiModes, ctx->dims[1], ctx->dims[2]};
+    const int inp[3] = {48, h1p, h2p};
+    const int outs[3] = {ctx->dims[1], ctx->dims[2], K};
+    const int outp[3] = {h1p, h2p, n3};
+    for (int l = 0; l < 3; ++l) {
+        const std::vector<double> &W = ctx->W[l];
+        auto w_at = [&](int n, int k) -> double { return (n < outs[l] && k < ins[l]) ? W[(size_t)n * ins[l] + k] : 0.0; };
+        add_image(outp[l], inp[l], [&](int n, int k) { return to_half_bits(w_at(n, k), fmt); });
+        if (split)
+            add_image(outp[l], inp[l], [&](int n, int k) {
+                const double v = w_at(n, k);
+                return to_half_bits(v - from_half_bits(to_half_bits(v, fmt), fmt), fmt);
+            });
+    }
+    const int n_mlp = (int)items.size();
+    while (items.size() < 6) items.push_back(Item{0, 0, 0, 0});
+    // folded bias PSF h_b = sum_k b3_k H_k as an exact hi/lo pair of rows K, K+1
+    std::vector<double> hb(T, 0.0);
+    for (int k = 0; k < K; ++k)
+        for (int t = 0; t < T; ++t) hb[t] += ctx->b[2][k] * ctx->H[(size_t)k * T + t];
+    auto basis_row = [&](int k, int t) -> uint16_t {
+        if (k < K) return to_half_bits(ctx->H[(size_t)k * T + t], fmt);
+        const uint16_t hi = to_half_bits(hb[t], fmt);
+        if (k == K) return hi;
+        if (k == K + 1) return to_half_bits(hb[t] - from_half_bits(hi, fmt), fmt);
+        return 0;
+    };
+    for (int c = 0; c < kMainChunks; ++c)
+        add_image(kMainN, kKP, [&](int n, int k) {
+            const int u = n / 32, ty = n % 32, tx = 3 * c + u;
+            return basis_row(k, ty * kTaps + tx);
+        });
+    add_image(kLastN, kKP, [&](int n, int k) { return n < kTaps ? basis_row(k, (kTaps - 1) * kTaps + n) : (uint16_t)0; });
+    std::vector<float> bias(h1p + h2p, 0.f);
+    for (int o = 0; o < ctx->dims[1]; ++o) bias[o] = (float)ctx->b[0][o];
+    for (int o = 0; o < ctx->dims[2]; ++o) bias[h1p + o] = (float)ctx->b[1][o];
+    std::vector<float> b3(K);
+    for (int k = 0; k < K; ++k) b3[k] = (float)ctx->b[2][k];
+    void *dstream = nullptr;
+    float *dbias = nullptr;
+    if (cudaMalloc(&dstream, buf.size()) != cudaSuccess ||
+        cudaMalloc(&dbias, (bias.size() + b3.size()) * sizeof(float)) != cudaSuccess) {
+        cudaFree(dstream);
+        set_error("device allocation failed for tensor-core operands");
+        return P2S_ENOMEM;
+    }
+    P2S_CUDA(cudaMemcpy(dstream, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(dbias, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice));
+    P2S_CUDA(cudaMemcpy(dbias + bias.size(), b3.data(), b3.size() * 4, cudaMemcpyHostToDevice));
+    ctx->tc.d_H = dstream;
+    ctx->tc.d_bias = dbias;
+    ctx->tc.H_bytes = buf.size();
+    static_assert(sizeof(Item) == 16, "item layout");
+    ctx->tc_items.assign((const uint8_t *)items.data(), (const uint8_t *)(items.data() + items.size()));
+    ctx->tc.n_mlp = n_mlp;
+    ctx->tc.h1p = h1p;
+    ctx->tc.h2p = h2p;
+    ctx->tc.n3 = n3;
+    ctx->tc.fmt = fmt;
+    ctx->tc.split = split;
+    ctx->tc.ready = 1;
+    return P2S_OK;
+}
+
+int tc_smem_bytes() { return kSmemBytes; }
+
+p2s_status launch_tc(p2s_ctx *ctx, int mode, const FieldGeom &g, int n, int C, const float *const *xw,
+                     float *const *y, const float *alpha, const float *beta_in, float *beta_out, int *status,
+                     cudaStream_t st) {
+    if (n <= 0) return P2S_OK;
+    p2s_status s0 = tc_prepare(ctx);
+    if (s0 != P2S_OK) return s0;
+    Params p;
+    std::memset(&p, 0, sizeof p);
+    for (int i = 0; i < n; ++i) {
+        p.xw[i] = xw ? xw[i] : nullptr;
+        p.y[i] = y ? y[i] : nullptr;
+    }
+    p.alpha = alpha;
+    p.beta_in = beta_in;
+    p.beta_out = beta_out;
+    p.stream = (const uint8_t *)ctx->tc.d_H;
+    p.bias = ctx->tc.d_bias;
+    p.b3 = ctx->tc.d_bias + ctx->tc.h1p + ctx->tc.h2p;
+    p.status = status;
+    p.n = n;
+    p.H = g.H;
+    p.W = g.W;
+    p.C = C;
+    p.s = g.s;
+    p.Ah = g.Ah;
+    p.Aw = g.Aw;
+    p.inv_s = 1.0f / (float)g.s;
+    p.K = ctx->K;
+    p.h1p = ctx->tc.h1p;
+    p.h2p = ctx->tc.h2p;
+    p.n3 = ctx->tc.n3;
+    p.mode = mode;
+    p.fold = mode == kFull ? 1 : 0;
+    p.ab_fmt = ctx->tc.fmt;
+    p.split = ctx->tc.split;
+    p.tiles_x = (g.W + kStrip - 1) / kStrip;
+    p.tiles_y = (g.H + kBand - 1) / kBand;
+    p.tiles_total = p.tiles_x * p.tiles_y * n;
+    p.n_mlp_items = ctx->tc.n_mlp;
+    std::memcpy(p.item, ctx->tc_items.data(), sizeof(p.item));
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const int grid = p.tiles_total < sms ? p.tiles_total : sms;
+    const double npx = (double)g.H * g.W * n;
+    double macs_net = 0.0;
+    for (int l = 0; l < 3; ++l) macs_net += (double)ctx->dims[l] * ctx->dims[l + 1];
+    const double flops = mode == kBlurOnly   ? 2.0 * ctx->K * ctx->T * npx
+                         : mode == kMlpOnly ? 2.0 * macs_net * npx
+                                            : 2.0 * (ctx->K * ctx->T + macs_net) * npx;
+    ProfScope pr(ctx, st, mode == kFull ? "fused_tc_gather" : mode == kMlpOnly ? "mlp_tc" : "blur_tc_gather", flops,
+                 npx * C * 8.0);
+    if (C == 3) {
+        P2S_CUDA(cudaFuncSetAttribute(fused_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        fused_kernel<3><<<grid, kThreads, kSmemBytes, st>>>(p);
+    } else {
+        P2S_CUDA(cudaFuncSetAttribute(fused_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        fused_kernel<1><<<grid, kThreads, kSmemBytes, st>>>(p);
+    }
+    P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+}  // namespace p2s

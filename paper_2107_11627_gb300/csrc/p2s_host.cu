@@ -225,7 +225,8 @@ p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr
     if (!(form == P2S_SCATTER || form == P2S_GATHER || form == P2S_FFT)) return einval("unknown blur form");
     if (!(precision == P2S_FP32 || precision == P2S_BF16 || precision == P2S_FP16 || precision == P2S_FP8E4M3))
         return einval("unknown precision");
-    if (precision != P2S_FP32 || form == P2S_FFT) {
+    const bool tc_prec = precision == P2S_BF16 || precision == P2S_FP16;
+    if (form == P2S_FFT || precision == P2S_FP8E4M3 || (tc_prec && form != P2S_GATHER)) {
         set_error("precision/form pair not built yet");
         return P2S_EUNSUPPORTED;
     }
@@ -313,6 +314,14 @@ p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr
             return fail(P2S_ECUDA);
         }
     }
+    if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+        set_error("device allocation failed in p2s_create");
+        return fail(P2S_ENOMEM);
+    }
+    if (tc_prec) {
+        p2s_status st = tc_prepare(ctx);
+        if (st != P2S_OK) return fail(st);
+    }
     // Keep stream-ordered scratch cached between calls.
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
@@ -341,10 +350,24 @@ void p2s_destroy(p2s_ctx *ctx) {
         cudaFree(kv.second.twiddle);
         cudaFree(kv.second.gain);
     }
+    cudaFree(ctx->d_status);
     cudaFree(ctx->tc.d_W);
     cudaFree(ctx->tc.d_H);
     cudaFree(ctx->tc.d_bias);
     delete ctx;
+}
+
+p2s_status p2s_check(p2s_ctx *ctx, void *stream) {
+    if (!ctx) return einval("ctx is NULL");
+    P2S_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int word = 0;
+    P2S_CUDA(cudaMemcpy(&word, ctx->d_status, sizeof word, cudaMemcpyDeviceToHost));
+    if (word != 0) {
+        P2S_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        set_error("a bounded device wait gave up (status word 0x%x)", word);
+        return P2S_ETIMEOUT;
+    }
+    return P2S_OK;
 }
 
 p2s_status p2s_profile(p2s_ctx *ctx, int enable) {
@@ -478,6 +501,9 @@ p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *
     FieldGeom g;
     p2s_status st = geometry(ctx, H, W, &g);
     if (st != P2S_OK) return st;
+    if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16)
+        return launch_tc(ctx, kTcMlpOnly, g, 1, 1, nullptr, nullptr, alpha, nullptr, beta, ctx->d_status,
+                         (cudaStream_t)stream);
     return launch_mlp_simt(ctx, g, 1, alpha, beta, (cudaStream_t)stream);
 }
 
@@ -489,6 +515,12 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
     if (xw->data == out->data) return einval("out must not alias xw");
     const float *ip[1] = {xw->data};
     float *op[1] = {out->data};
+    if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) {
+        FieldGeom g;
+        if ((st = geometry(ctx, xw->H, xw->W, &g)) != P2S_OK) return st;
+        return launch_tc(ctx, kTcBlurOnly, g, 1, xw->C, ip, op, nullptr, beta, nullptr, ctx->d_status,
+                         (cudaStream_t)stream);
+    }
     return launch_blur_simt(ctx, xw->H, xw->W, xw->C, 1, ip, beta, op, ctx->form, (cudaStream_t)stream);
 }
 
@@ -501,9 +533,10 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
     p2s_status st = geometry(ctx, H, W, &g);
     if (st != P2S_OK) return st;
     const size_t npx = (size_t)H * W;
+    const bool tc = ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16;
     // bound the FP32 path's beta scratch to ~1 GiB per launch group
     int chunk = kMaxBatch;
-    const size_t beta_px = npx * ctx->K * sizeof(float);
+    const size_t beta_px = tc ? 0 : npx * ctx->K * sizeof(float);
     while (chunk > 1 && (size_t)chunk * beta_px > (1ull << 30)) chunk /= 2;
     for (int i0 = 0; i0 < n; i0 += chunk) {
         const int nb = n - i0 < chunk ? n - i0 : chunk;
@@ -538,8 +571,12 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
         }
         st = launch_fields(ctx, g, fb, alpha, fscr, s);
         if (st == P2S_OK) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
-        if (st == P2S_OK) st = launch_mlp_simt(ctx, g, nb, alpha, beta, s);
-        if (st == P2S_OK) st = launch_blur_simt(ctx, H, W, C, nb, xwp, beta, op, ctx->form, s);
+        if (tc) {
+            if (st == P2S_OK) st = launch_tc(ctx, kTcFull, g, nb, C, xwp, op, alpha, nullptr, nullptr, ctx->d_status, s);
+        } else {
+            if (st == P2S_OK) st = launch_mlp_simt(ctx, g, nb, alpha, beta, s);
+            if (st == P2S_OK) st = launch_blur_simt(ctx, H, W, C, nb, xwp, beta, op, ctx->form, s);
+        }
         cudaFreeAsync(scratch, s);
         if (st != P2S_OK) return st;
     }

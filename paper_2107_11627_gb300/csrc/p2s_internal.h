@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <map>
 #include <string>
 #include <vector>
@@ -51,10 +52,11 @@ struct FilterTable {
 
 // Tensor-core operand packs (filled by the tcgen05 translation unit).
 struct TcPack {
-    void *d_W = nullptr;      // packed network weights (canonical smem image)
-    void *d_H = nullptr;      // packed basis chunks (canonical smem image)
-    float *d_bias = nullptr;  // FP32 biases
+    void *d_W = nullptr;      // unused (weights live in the stream below)
+    void *d_H = nullptr;      // stream of B images: network weights, then basis chunks
+    float *d_bias = nullptr;  // FP32 b1, b2, b3
     size_t W_bytes = 0, H_bytes = 0;
+    int n_mlp = 0, h1p = 0, h2p = 0, n3 = 0, fmt = 0, split = 0;
     int ready = 0;
 };
 
@@ -92,6 +94,8 @@ struct p2s_ctx {
     int *d_kernel_of_mode = nullptr;
     std::map<int, p2s::FilterTable> tables;
     p2s::TcPack tc;
+    std::vector<uint8_t> tc_items;  // item table of the tensor-core stream (opaque here)
+    int *d_status = nullptr;        // device status word of bounded waits
     // staging for p2s_simulate_host
     void *stage = nullptr;
     size_t stage_bytes = 0;
@@ -135,5 +139,12 @@ p2s_status launch_mlp_simt(const p2s_ctx *ctx, const FieldGeom &g, int n, const 
                            cudaStream_t st);
 p2s_status launch_blur_simt(const p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw,
                             const float *beta, float *const *y, p2s_blur_form form, cudaStream_t st);
+
+// tensor-core path (k_tc.cu)
+p2s_status tc_prepare(p2s_ctx *ctx);
+p2s_status launch_tc(p2s_ctx *ctx, int mode, const FieldGeom &g, int n, int C, const float *const *xw,
+                     float *const *y, const float *alpha, const float *beta_in, float *beta_out, int *status,
+                     cudaStream_t st);
+constexpr int kTcFull = 0, kTcMlpOnly = 1, kTcBlurOnly = 2;
 
 }  // namespace p2s

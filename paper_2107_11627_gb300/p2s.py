@@ -67,6 +67,7 @@ _SIGS = {
     "p2s_stage_mlp": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_stage_blur": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
     "p2s_noll_covariance": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "p2s_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "p2s_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "p2s_profile_read": (C.c_int, [C.c_void_p, C.POINTER(p2s_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
 }
@@ -177,6 +178,10 @@ class Simulator:
             self.close()
         except Exception:
             pass
+
+    def check(self, stream=None):
+        """Synchronise and raise if a device-side bounded wait gave up since the last check."""
+        _check(lib().p2s_check(self.ctx, _stream_handle(stream)), "p2s_check")
 
     def profile(self, enable: bool):
         """Start (clearing) or stop per-kernel event timing."""

@@ -82,3 +82,13 @@ def test_stage_calls_reject_null(lib):
 
     assert lib.p2s_stage_noise(None, 0, 0, 4, 4, None, None) == p2s.P2S_EINVAL
     assert lib.p2s_simulate(None, None, 0, None, None, None, None) == p2s.P2S_EINVAL
+
+
+def test_product_basis_builder_matches_oracle():
+    from oracle import psf
+    from paper_2107_11627_gb300 import basis, inputs
+
+    z, dr0 = inputs.dictionary_draws(600, 35, (0.5, 6.0), 2021)
+    Ho, _ = psf.make_basis(z, dr0, K=12, taps=9)
+    Hp = basis.build_basis(12, 9, 600, cache=False)
+    assert np.max(np.abs(Ho - Hp)) < 1e-12

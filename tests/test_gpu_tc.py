@@ -1,0 +1,100 @@
+"""GPU parity of the tensor-core path (tcgen05): the network stage, the blur
+stage and whole frames against the FP64 oracle, FP16 and BF16 operands."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.fields import CorrParams
+from oracle.precision import bf16
+from paper_2107_11627_gb300 import inputs
+
+from gpu_common import TOL_BF16, cfg2, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _sim(prec, form="gather", s=8):
+    from paper_2107_11627_gb300 import p2s
+
+    c = cfg2()
+    return p2s.Simulator(c["H"], c["taps"], c["layers"], anchor_spacing=s, corr_len_px=(16.0,), precision=prec,
+                         form=form)
+
+
+def _alpha_f32(seed, dr, h, w, s=8):
+    a = oracle.fields.alpha_anchors(seed, dr, h, w, CorrParams(s, (16.0,))).astype(np.float32)
+    full = np.zeros(a.shape[:2] + (36,), dtype=np.float32)
+    full[..., 1:] = a
+    return full
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("h,w", [(64, 128), (37, 150), (2, 3)])
+def test_tc_network_stage(prec, h, w):
+    sim = _sim(prec)
+    al = _alpha_f32(21, 4.0, h, w)
+    beta = sim.stage_mlp(h, w, torch.from_numpy(al).cuda())
+    sim.check()
+    beta = beta.cpu().numpy()
+    ap = oracle.fields.alpha_pixels(al[..., 1:].astype(np.float64), h, w, 8)
+    ref = oracle.mlp.forward(ap[..., 2:], cfg2()["layers"])
+    assert rel(beta, ref) < TOL_BF16, rel(beta, ref)
+
+
+@pytest.mark.parametrize("c", [3, 1])
+@pytest.mark.parametrize("h,w", [(40, 130), (33, 64), (1, 1), (70, 300)])
+def test_tc_blur_stage_fp16(c, h, w):
+    sim = _sim("fp16")
+    rng = np.random.default_rng(31)
+    xw = inputs.blob_image(h, w, c, 1003)
+    beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
+    y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda())
+    sim.check()
+    y = y.cpu().numpy()
+    ref = oracle.blur.gather(xw.astype(np.float64), beta.astype(np.float64), cfg2()["H"], 33, 33)
+    assert rel(y, ref) < TOL_BF16, rel(y, ref)
+
+
+def test_tc_blur_stage_bf16_rounding_points():
+    """BF16 operands: the kernel must round exactly beta and H to BF16 (checked
+    against the oracle with those two tensors rounded), everything else FP32."""
+    sim = _sim("bf16")
+    rng = np.random.default_rng(32)
+    h, w = 48, 160
+    xw = inputs.blob_image(h, w, 3, 1004)
+    beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
+    y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
+    emu = oracle.blur.gather(xw.astype(np.float64), bf16(beta), bf16(cfg2()["H"]), 33, 33)
+    assert rel(y, emu) < 2e-5, rel(y, emu)
+
+
+@pytest.mark.parametrize("s", [8, 1])
+def test_tc_frames_fp16(s):
+    sim = _sim("fp16", s=s)
+    shapes = [(96, 80), (50, 200), (96, 80)]
+    xs = [inputs.blob_image(h, w, 3, 1000 + i) for i, (h, w) in enumerate(shapes)]
+    dr, seeds = [1.5, 4.0, 6.0], [10**6, 10**6 + 1, 10**6 + 2]
+    ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
+    sim.check()
+    for i in range(3):
+        ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
+                                    CorrParams(s, (16.0,)), (33, 33), form="gather")
+        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_BF16, (i, rel(ys[i].cpu().numpy(), ref.y))
+
+
+def test_tc_full_size_frame_fp16():
+    """One 512 x 512 RGB frame of the benchmark workload, whole frame checked."""
+    sim = _sim("fp16")
+    x = inputs.blob_image(512, 512, 3, 1000)
+    (y,) = sim.simulate([torch.from_numpy(x).cuda()], [3.0], [10**6])
+    ref = oracle.frame.simulate(x.astype(np.float64), 10**6, 3.0, cfg2()["H"], cfg2()["layers"],
+                                CorrParams(8, (16.0,)), (33, 33), form="gather")
+    assert rel(y.cpu().numpy(), ref.y) < TOL_BF16
