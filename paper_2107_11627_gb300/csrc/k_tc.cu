@@ -115,9 +115,10 @@ struct Ctl {
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Ctl &ctl, int code) {
     if (ptx::mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
-    while (true) {
+    for (int spins = 0;; ++spins) {
         if (ptx::mbar_try(bar, parity)) return true;
         if (*ctl.abort) return false;
+        if (spins > 4) __nanosleep(spins < 64 ? 32 : 128);  // leave issue slots to working warps
         if (clock64() - t0 > 4000000000ll) {
             *ctl.abort = 1;
             atomicOr(ctl.status, code);
@@ -165,8 +166,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
         ptx::mbar_init(BAR(kBetab), 8);
         ptx::mbar_init(BAR(kDFull0), 1);
         ptx::mbar_init(BAR(kDFull0 + 1), 1);
-        ptx::mbar_init(BAR(kDEmpty0), 4);
-        ptx::mbar_init(BAR(kDEmpty0 + 1), 4);
+        ptx::mbar_init(BAR(kDEmpty0), 8);
+        ptx::mbar_init(BAR(kDEmpty0 + 1), 8);
         ptx::mbar_fence_init();
     }
     for (int i = threadIdx.x; i < p.h1p + p.h2p; i += blockDim.x) sbias[i] = p.bias[i];
@@ -241,12 +242,15 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                                     ptx::fence_after();
                                     const uint32_t idesc = ptx::idesc_f16(p.ab_fmt, (int)itm.n);
                                     const int ksteps = (int)itm.k / 16;
-                                    for (int r = 0; r < 2; ++r)
-                                        for (int ks = 0; ks < ksteps; ++ks) {
-                                            const uint64_t bd = ptx::smem_desc(sa + ks * 2 * (itm.n * 16), itm.n * 16, 128);
-                                            ptx::mma_ts(tmem + d_reg[L][r], tmem + a_reg[L][r] + ks * 8, bd, idesc,
-                                                        (w > 0 || ks > 0) ? 1u : 0u);
-                                        }
+                                    const uint64_t bd = ptx::smem_desc(sa, itm.n * 16, 128);
+                                    const uint64_t bstep = (uint64_t)(2 * itm.n);  // 2 core-matrix columns, 16-byte units
+                                    const uint32_t d0 = tmem + d_reg[L][0], d1 = tmem + d_reg[L][1];
+                                    const uint32_t a0 = tmem + a_reg[L][0], a1 = tmem + a_reg[L][1];
+                                    for (int ks = 0; ks < ksteps; ++ks) {
+                                        const uint32_t acc = (w > 0 || ks > 0) ? 1u : 0u;
+                                        ptx::mma_ts(d0, a0 + ks * 8, bd + ks * bstep, idesc, acc);
+                                        ptx::mma_ts(d1, a1 + ks * 8, bd + ks * bstep, idesc, acc);
+                                    }
                                 }
                                 ptx::mma_commit(BAR(kEmpty0 + slot));
                             }
@@ -265,12 +269,15 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                             if (brdy && sa && free_buf) {
                                 const uint32_t n = p.item[6 + c].n;
                                 const uint32_t idesc = (n == (uint32_t)kMainN) ? idesc_n96 : idesc_n48;
-                                for (int r = 0; r < 2; ++r)
-                                    for (int ks = 0; ks < kKSteps; ++ks) {
-                                        const uint64_t bd = ptx::smem_desc(sa + ks * 2 * (n * 16), n * 16, 128);
-                                        ptx::mma_ts(tmem + colDB(h) + r * kMainN, tmem + colBeta(r) + ks * 8, bd, idesc,
-                                                    ks > 0 ? 1u : 0u);
-                                    }
+                                const uint64_t bd = ptx::smem_desc(sa, n * 16, 128);
+                                const uint64_t bstep = (uint64_t)(2 * n);
+                                const uint32_t d0 = tmem + colDB(h), d1 = d0 + kMainN;
+                                const uint32_t a0 = tmem + colBeta(0), a1 = tmem + colBeta(1);
+#pragma unroll
+                                for (int ks = 0; ks < kKSteps; ++ks) {
+                                    ptx::mma_ts(d0, a0 + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
+                                    ptx::mma_ts(d1, a1 + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
+                                }
                             }
                             ptx::mma_commit(BAR(kEmpty0 + slot));
                             ptx::mma_commit(BAR(kDFull0 + h));
@@ -444,76 +451,95 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                     if (lane == 0) ptx::mbar_arrive(BAR(kBetab));
                 }
                 if (!do_blur) continue;
-                // ---- contraction chunks: this half takes chunks c with c % 2 == half ----
+                // ---- contraction chunks: every warp takes every chunk; half h covers
+                //      tap rows [16h, 16h + 16) of each tap column (the last tap row:
+                //      tap columns [17h, 17h + 17 - h)) ----
                 float acc[2][3];
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) acc[i][ch] = 0.f;
-                const uint32_t buf = lane_base + colDB(half);
-                for (int c = half; c < kChunks; c += 2) {
-                    const bool got = __all_sync(0xffffffffu, wait_bar(BAR(kDFull0 + half), uses & 1, ctl, 128));
+                const int jlo = 16 - 16 * half;  // first window row (relative to tile row 2rp + 1)
+                for (int c = 0; c < kChunks; ++c) {
+                    const int b = c & 1;
+                    const uint32_t buf = lane_base + colDB(b);
+                    const bool got = __all_sync(0xffffffffu, wait_bar(BAR(kDFull0 + b), (uses >> b) & 1 ? 1u : 0u, ctl, 128));
+                    // uses holds one parity bit per buffer
+                    uses ^= (1u << b);
                     ok = ok && got;
                     ptx::fence_after();
                     if (!got) {
                     } else if (c < kMainChunks) {
+                        uint32_t g0[16], g1[16];
+                        ptx::tmem_ld16(buf + 16 * half, g0);
+                        ptx::tmem_ld16(buf + kMainN + 16 * half, g1);
 #pragma unroll 1
                         for (int u3 = 0; u3 < 3; ++u3) {
                             const int txx = 3 * c + u3;  // tap column 0..32
-                            uint32_t g0[32], g1[32];
-                            ptx::tmem_ld32(buf + 32 * u3, g0);
-                            ptx::tmem_ld32(buf + kMainN + 32 * u3, g1);
-                            float wr[33], wg[33], wb[33];
-                            const int base = (2 * rp + 1) * kTC + col + 32 - txx;
+                            float wr[17], wg[17], wb[17];
+                            const int base = (2 * rp + 1 + jlo) * kTC + col + 32 - txx;
 #pragma unroll
-                            for (int j = 0; j < 33; ++j) {
-                                const float2 rg = xrg[base + j * kTC];
-                                wr[j] = rg.x;
-                                wg[j] = rg.y;
-                                wb[j] = (C == 3) ? xb[base + j * kTC] : 0.f;
+                            for (int m = 0; m < 17; ++m) {
+                                const float2 rg = xrg[base + m * kTC];
+                                wr[m] = rg.x;
+                                wg[m] = rg.y;
+                                wb[m] = (C == 3) ? xb[base + m * kTC] : 0.f;
                             }
                             ptx::tmem_wait_ld();
+                            float a[16], bb[16];
 #pragma unroll
-                            for (int t = 0; t < 32; ++t) {
-                                const float a = __uint_as_float(g0[t]), b = __uint_as_float(g1[t]);
-                                acc[0][0] = fmaf(a, wr[31 - t], acc[0][0]);
-                                acc[1][0] = fmaf(b, wr[32 - t], acc[1][0]);
+                            for (int t = 0; t < 16; ++t) {
+                                a[t] = __uint_as_float(g0[t]);
+                                bb[t] = __uint_as_float(g1[t]);
+                            }
+                            if (u3 < 2) {  // next tap column's G while this one computes
+                                ptx::tmem_ld16(buf + 32 * (u3 + 1) + 16 * half, g0);
+                                ptx::tmem_ld16(buf + kMainN + 32 * (u3 + 1) + 16 * half, g1);
+                            }
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                // tap row ty = 16 half + t: window rows 15 - t (row 0), 16 - t (row 1)
+                                acc[0][0] = fmaf(a[t], wr[15 - t], acc[0][0]);
+                                acc[1][0] = fmaf(bb[t], wr[16 - t], acc[1][0]);
                                 if (C == 3) {
-                                    acc[0][1] = fmaf(a, wg[31 - t], acc[0][1]);
-                                    acc[0][2] = fmaf(a, wb[31 - t], acc[0][2]);
-                                    acc[1][1] = fmaf(b, wg[32 - t], acc[1][1]);
-                                    acc[1][2] = fmaf(b, wb[32 - t], acc[1][2]);
+                                    acc[0][1] = fmaf(a[t], wg[15 - t], acc[0][1]);
+                                    acc[0][2] = fmaf(a[t], wb[15 - t], acc[0][2]);
+                                    acc[1][1] = fmaf(bb[t], wg[16 - t], acc[1][1]);
+                                    acc[1][2] = fmaf(bb[t], wb[16 - t], acc[1][2]);
                                 }
                             }
                         }
-                    } else {
-                        // last tap row (dy = +16): 33 tap columns, source rows 2rp + i of the tile
-                        uint32_t g0[48], g1[48];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            ptx::tmem_ld16(buf + 16 * q, *reinterpret_cast<uint32_t(*)[16]>(&g0[16 * q]));
-                            ptx::tmem_ld16(buf + kMainN + 16 * q, *reinterpret_cast<uint32_t(*)[16]>(&g1[16 * q]));
-                        }
                         ptx::tmem_wait_ld();
+                    } else {
+                        // last tap row (dy = +16): source tile rows 2rp + i
+                        uint32_t g0[17], g1[17];
+                        ptx::tmem_ld16(buf + 17 * half, *reinterpret_cast<uint32_t(*)[16]>(&g0[0]));
+                        ptx::tmem_ld16(buf + kMainN + 17 * half, *reinterpret_cast<uint32_t(*)[16]>(&g1[0]));
+                        ptx::tmem_ld1(buf + 17 * half + 16, g0[16]);
+                        ptx::tmem_ld1(buf + kMainN + 17 * half + 16, g1[16]);
+                        ptx::tmem_wait_ld();
+                        const int ntx = half ? 16 : 17;
 #pragma unroll
-                        for (int txx = 0; txx < kTaps; ++txx) {
-                            const int i0 = (2 * rp) * kTC + col + 32 - txx, i1 = i0 + kTC;
-                            const float a = __uint_as_float(g0[txx]), b = __uint_as_float(g1[txx]);
-                            const float2 rg0 = xrg[i0], rg1 = xrg[i1];
-                            acc[0][0] = fmaf(a, rg0.x, acc[0][0]);
-                            acc[1][0] = fmaf(b, rg1.x, acc[1][0]);
-                            if (C == 3) {
-                                acc[0][1] = fmaf(a, rg0.y, acc[0][1]);
-                                acc[0][2] = fmaf(a, xb[i0], acc[0][2]);
-                                acc[1][1] = fmaf(b, rg1.y, acc[1][1]);
-                                acc[1][2] = fmaf(b, xb[i1], acc[1][2]);
+                        for (int q = 0; q < 17; ++q) {
+                            if (q < ntx) {
+                                const int txx = 17 * half + q;
+                                const int i0 = (2 * rp) * kTC + col + 32 - txx, i1 = i0 + kTC;
+                                const float a = __uint_as_float(g0[q]), b2 = __uint_as_float(g1[q]);
+                                const float2 rg0 = xrg[i0], rg1 = xrg[i1];
+                                acc[0][0] = fmaf(a, rg0.x, acc[0][0]);
+                                acc[1][0] = fmaf(b2, rg1.x, acc[1][0]);
+                                if (C == 3) {
+                                    acc[0][1] = fmaf(a, rg0.y, acc[0][1]);
+                                    acc[0][2] = fmaf(a, xb[i0], acc[0][2]);
+                                    acc[1][1] = fmaf(b2, rg1.y, acc[1][1]);
+                                    acc[1][2] = fmaf(b2, xb[i1], acc[1][2]);
+                                }
                             }
                         }
                     }
                     ptx::fence_before();
                     __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(BAR(kDEmpty0 + half));
-                    ++uses;
+                    if (lane == 0) ptx::mbar_arrive(BAR(kDEmpty0 + b));
                 }
                 // ---- combine the halves, write the row pair ----
                 if (half == 1) {

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/p2s.h"
+#include "p2s.h"
 
 namespace p2s {
 
