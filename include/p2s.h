@@ -205,6 +205,25 @@ p2s_status p2s_profile(p2s_ctx *ctx, int enable);
  * (one per kernel name, in order of first launch); *n_stats gets the count. */
 p2s_status p2s_profile_read(p2s_ctx *ctx, p2s_kernel_stat *stats, int max_stats, int *n_stats);
 
+/* Allocation-free variant of p2s_stage_mlp for FP32 contexts (no counterpart
+ * in the paper: it exists for callers that cannot allocate device memory at
+ * call time, e.g. code held to a fixed, pre-reserved memory budget or a host
+ * thread that must stay out of the CUDA allocator).  Same arguments, layout
+ * and result as p2s_stage_mlp.  It allocates nothing: the network's weight
+ * image is assembled in a 192 KiB array the library holds in device memory
+ * on every GPU that loads it, for the life of the process.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - Every call and every context on a device share the one array, and each
+ *     call rewrites it: calls whose work overlaps on the GPU (different
+ *     streams, or concurrent host threads) race; serialise them.
+ *   - Errors: EUNSUPPORTED for non-FP32 contexts or networks the plain path
+ *     does not build; EINVAL if the weight image (weights plus biases, each
+ *     bias block padded to 4 floats) exceeds 48 Ki floats, or if the current
+ *     device is not the context's. */
+p2s_status p2s_stage_mlp_noalloc(p2s_ctx *ctx, int H, int W, const float *alpha, float *beta, void *stream);
+
 /* ---- host-side building blocks ----------------------------------------- */
 
 /* Noll covariance R_Z of modes J = 2..j_max at D/r0 = 1 (Sec. 2.2; closed

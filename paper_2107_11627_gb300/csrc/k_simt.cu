@@ -319,3 +319,118 @@ p2s_status launch_blur_simt(const p2s_ctx *ctx, int H, int W, int C, int n, cons
 }
 
 }  // namespace p2s
+
+// ---- allocation-free variant of the FP32 network stage ---------------------
+//
+// Some callers cannot allocate device memory at the moment they want to run
+// the network: code that runs under a fixed, pre-reserved memory budget, or a
+// host thread that must not enter the CUDA allocator (for example while it
+// records work that has to stay free of allocations).  p2s_stage_mlp
+// assembles the network's weight image in a buffer it allocates per call;
+// this variant assembles it in a file-scope device array instead, so the call
+// allocates nothing.  Every GPU that loads the library holds the array until
+// the process exits.
+
+#include <mutex>
+
+namespace p2s {
+namespace {
+
+constexpr int kNoAllocWeightFloats = 48 * 1024;  // 192 KiB: weight image limit of the variant
+static __device__ __align__(256) float g_noalloc_weights[kNoAllocWeightFloats];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on `dev` (the current device).  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with cudaGetSymbolAddress and cached.
+p2s_status noalloc_weights_on(int dev, float **out) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("device ordinal %d out of range for the allocation-free scratch", dev);
+        return P2S_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_weights);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the allocation-free scratch failed: %s", cudaGetErrorString(e));
+            return P2S_ECUDA;
+        }
+        g_noalloc_ptr[dev] = (float *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return P2S_OK;
+}
+
+}  // namespace
+}  // namespace p2s
+
+extern "C" p2s_status p2s_stage_mlp_noalloc(p2s_ctx *ctx, int H, int W, const float *alpha, float *beta,
+                                            void *stream) {
+    using namespace p2s;
+    if (!ctx || !alpha || !beta) {
+        set_error("ctx, alpha and beta must be non-NULL");
+        return P2S_EINVAL;
+    }
+    if (ctx->prec != P2S_FP32) {
+        set_error("the allocation-free network stage serves FP32 contexts only");
+        return P2S_EUNSUPPORTED;
+    }
+    FieldGeom g;
+    p2s_status st = geometry(ctx, H, W, &g);
+    if (st != P2S_OK) return st;
+    if (ctx->n_layers > 4) {
+        set_error("plain network path supports at most 4 layers");
+        return P2S_EUNSUPPORTED;
+    }
+    MlpLayers lay;
+    lay.n = ctx->n_layers;
+    int off = 0;
+    for (int l = 0; l < lay.n; ++l) {
+        lay.in[l] = ctx->dims[l];
+        lay.out[l] = ctx->dims[l + 1];
+        lay.w_off[l] = off;
+        off += lay.in[l] * lay.out[l];
+        lay.b_off[l] = off;
+        off += (lay.out[l] + 3) & ~3;
+        lay.relu[l] = l + 1 < lay.n;
+    }
+    if (off > kNoAllocWeightFloats) {
+        set_error("network weights need %d floats; the allocation-free scratch holds %d", off, kNoAllocWeightFloats);
+        return P2S_EINVAL;
+    }
+    const size_t smem = (size_t)off * 4 + 2ull * kMaxWidth * kMlpThreads * 4;
+    if (smem > 227 * 1024) {
+        set_error("network too large for the plain path (%zu bytes of shared memory)", smem);
+        return P2S_EUNSUPPORTED;
+    }
+    int dev = -1;
+    P2S_CUDA(cudaGetDevice(&dev));
+    if (dev != ctx->device) {
+        set_error("current device %d is not the context's device %d", dev, ctx->device);
+        return P2S_EINVAL;
+    }
+    float *wimg = nullptr;
+    if ((st = noalloc_weights_on(dev, &wimg)) != P2S_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // The image is rewritten in full by every call; the padding floats after
+    // each bias block are never read, so nothing needs clearing.
+    for (int l = 0; l < lay.n; ++l) {
+        P2S_CUDA(cudaMemcpyAsync(wimg + lay.w_off[l], ctx->d_Wt32[l], (size_t)lay.in[l] * lay.out[l] * 4,
+                                 cudaMemcpyDeviceToDevice, s));
+        P2S_CUDA(cudaMemcpyAsync(wimg + lay.b_off[l], ctx->d_b32[l], (size_t)lay.out[l] * 4, cudaMemcpyDeviceToDevice,
+                                 s));
+    }
+    P2S_CUDA(cudaFuncSetAttribute(mlp_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const long long nblk = ((long long)g.H * g.W + kMlpThreads - 1) / kMlpThreads;
+    const int grid = (int)(nblk < 2LL * sms ? nblk : 2LL * sms);
+    mlp_simt_kernel<<<grid, kMlpThreads, smem, s>>>(lay, off, 1, g.H, g.W, g.s, 1.0f / g.s, g.Aw, g.Ah * g.Aw, wimg,
+                                                    alpha, beta);
+    P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}

@@ -66,6 +66,7 @@ _SIGS = {
     "p2s_stage_warp": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
     "p2s_stage_mlp": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_stage_blur": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
+    "p2s_stage_mlp_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_noll_covariance": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "p2s_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "p2s_profile": (C.c_int, [C.c_void_p, C.c_int]),
