@@ -63,7 +63,7 @@ class ClockSampler:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -115,16 +115,20 @@ def dist():
     return None, rank, world, local
 
 
-def oracle_frame_time(H, layers, x, dr, seed, rows=None):
-    """Seconds the FP64 oracle takes for frame x (or its first `rows` rows)."""
+def oracle_frame(H, layers, x, dr, seed, rows=None, form="scatter"):
+    """(seconds, output) of the FP64 oracle for frame x (or its first `rows` rows)."""
     import oracle
 
     if rows is not None:
         x = x[:rows]
     t0 = time.perf_counter()
-    oracle.frame.simulate(x.astype(np.float64), seed, dr, H, layers, oracle.fields.CorrParams(8, (16.0,)),
-                          (TAPS, TAPS))
-    return time.perf_counter() - t0
+    y = oracle.frame.simulate(x.astype(np.float64), seed, dr, H, layers, oracle.fields.CorrParams(8, (16.0,)),
+                              (TAPS, TAPS), form=form).y
+    return time.perf_counter() - t0, y
+
+
+def oracle_frame_time(H, layers, x, dr, seed, rows=None, form="scatter"):
+    return oracle_frame(H, layers, x, dr, seed, rows, form)[0]
 
 
 def run_reference(args):
@@ -161,10 +165,10 @@ def main():
     global N_FRAMES
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp16", "fp32", "fp8"])
-    ap.add_argument("--form", default="scatter", choices=["scatter", "gather", "fft"])
+    ap.add_argument("--precision", default="fp16", choices=["bf16", "fp16", "fp32", "fp8"])
+    ap.add_argument("--form", default="gather", choices=["scatter", "gather", "fft"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=128, help="rows per step of the reference arm's sample")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -274,11 +278,16 @@ def main():
         e2e = {"value": N_FRAMES * args.e2e_steps * world / el, "unit": "frames/s",
                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step}
 
-    cpu = None
+    cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t = oracle_frame_time(Hb, layers, xs_host[0], float(dr[0]), int(seeds[0]))
+        form = args.form if args.form in ("scatter", "gather") else "scatter"
+        t, y_ref = oracle_frame(Hb, layers, xs_host[0], float(dr[0]), int(seeds[0]), form=form)
         cpu = {"value": 1.0 / t, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"frame 0 of the batch ({HW}x{HW}x3), full path, FP64 NumPy, one run"}
+        y_gpu = ys[0].cpu().numpy().astype(np.float64)
+        err = y_gpu - y_ref
+        acc = {"frame": 0, "vs": "FP64 oracle", "rel_l2": float(np.linalg.norm(err) / np.linalg.norm(y_ref)),
+               "max_abs": float(np.abs(err).max())}
 
     if rank == 0:
         dtype = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision]
@@ -293,7 +302,7 @@ def main():
                 "latency_ms": {"step_p50": float(np.percentile(step_ms, 50)),
                                "step_p99": float(np.percentile(step_ms, 99)),
                                "frame_p50": float(np.percentile(step_ms, 50)) / N_FRAMES},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in kstats]}
         print(json.dumps(line), flush=True)
     sim.close()
