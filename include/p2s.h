@@ -171,6 +171,15 @@ p2s_status p2s_stage_warp(p2s_ctx *ctx, const p2s_image *in, const float *alpha,
  * frame), device float32 [H][W][K], in the context's precision. */
 p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *beta, void *stream);
 
+/* Steps 2 + 4 for FP16 / BF16 contexts, written the way the tensor-core blur
+ * reads beta: the 16-bit operand layout beta16[H][14][W][8] (device, 16-bit
+ * FP16 or BF16 values as the context's precision, H*W*224 bytes), where
+ * element (row, g, col, e) is beta_k of pixel (row, col) for k = 8 g + e.
+ * It holds the network output WITHOUT the last layer's bias (Sec. 3.3 network
+ * with b3 folded into the basis as an exact hi/lo pair of extra rows): entries
+ * k = K and K + 1 are 1.0, entries beyond are 0.  EUNSUPPORTED for FP32. */
+p2s_status p2s_stage_mlp16(p2s_ctx *ctx, int H, int W, const float *alpha, void *beta16, void *stream);
+
 /* Step 5 alone: y = blur of x_w with per-pixel weights beta (device float32
  * [H][W][K]) in the context's form and precision (beta is rounded to the
  * operand type first). */
@@ -183,6 +192,17 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
  * was set (the outputs of the calls since the last check are then invalid),
  * P2S_ECUDA if the stream reports an error, P2S_OK otherwise. */
 p2s_status p2s_check(p2s_ctx *ctx, void *stream);
+
+/* ---- tuning --------------------------------------------------------------- */
+
+/* Tunable launch parameters (no counterpart in the paper; results do not
+ * depend on them beyond floating-point summation order):
+ *   P2S_OPT_SCATTER_SEGMENT_ROWS  source rows per work unit of the
+ *       tensor-core scatter blur (even, >= 2; 0 = default 128).  Target rows
+ *       within 16 rows of a segment boundary are summed with atomic adds. */
+typedef enum { P2S_OPT_SCATTER_SEGMENT_ROWS = 1 } p2s_option;
+p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value);
+p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value);
 
 /* ---- kernel timing ------------------------------------------------------- */
 

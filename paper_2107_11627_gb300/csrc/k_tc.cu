@@ -27,6 +27,7 @@
 #include <cstring>
 
 #include "p2s_internal.h"
+#include "tc_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace p2s {
@@ -95,45 +96,10 @@ constexpr int kOffMisc = kOffBar + kNBar * 8;                  // tmem base, abo
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;               // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
-__device__ __forceinline__ uint32_t pack2(float a, float b, int fmt) {
-    if (fmt == 1) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<uint32_t *>(&h);
-    }
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-struct Ctl {
-    volatile int *abort;
-    int *status;
-};
-
-// Bounded wait (about 2 s at 2 GHz); on timeout flags the CTA and the status
-// word.  Once the CTA is flagged every wait returns false at once, so all
-// roles run their (data-independent) loops to the end and meet at teardown.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Ctl &ctl, int code) {
-    if (ptx::mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (int spins = 0;; ++spins) {
-        if (ptx::mbar_try(bar, parity)) return true;
-        if (*ctl.abort) return false;
-        if (spins > 4) __nanosleep(spins < 64 ? 32 : 128);  // leave issue slots to working warps
-        if (clock64() - t0 > 4000000000ll) {
-            *ctl.abort = 1;
-            atomicOr(ctl.status, code);
-            return false;
-        }
-    }
-}
-
-// Bounded wait that ignores the abort flag: used to let issued bulk copies
-// land before the CTA's shared memory is released.
-__device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!ptx::mbar_try(bar, parity) && clock64() - t0 < 4000000000ll) {
-    }
-}
+using tcc::Ctl;
+using tcc::drain_bar;
+using tcc::pack2;
+using tcc::wait_bar;
 
 template <int C>
 __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constant__ Params p) {

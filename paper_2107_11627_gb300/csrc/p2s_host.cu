@@ -226,7 +226,7 @@ p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr
     if (!(precision == P2S_FP32 || precision == P2S_BF16 || precision == P2S_FP16 || precision == P2S_FP8E4M3))
         return einval("unknown precision");
     const bool tc_prec = precision == P2S_BF16 || precision == P2S_FP16;
-    if (form == P2S_FFT || precision == P2S_FP8E4M3 || (tc_prec && form != P2S_GATHER)) {
+    if (form == P2S_FFT || precision == P2S_FP8E4M3) {
         set_error("precision/form pair not built yet");
         return P2S_EUNSUPPORTED;
     }
@@ -354,6 +354,7 @@ void p2s_destroy(p2s_ctx *ctx) {
     cudaFree(ctx->tc.d_W);
     cudaFree(ctx->tc.d_H);
     cudaFree(ctx->tc.d_bias);
+    cudaFree(ctx->tc.d_Hs);
     delete ctx;
 }
 
@@ -506,6 +507,34 @@ p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *
                          (cudaStream_t)stream);
     return launch_mlp_simt(ctx, g, 1, alpha, beta, (cudaStream_t)stream);
 }
+p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
+    if (!ctx) return einval("ctx must be non-NULL");
+    if (option == P2S_OPT_SCATTER_SEGMENT_ROWS) {
+        if (value != 0 && (value < 2 || (value & 1))) return einval("segment rows must be 0 or an even number >= 2");
+        ctx->tc.seg_rows = value;
+        return P2S_OK;
+    }
+    return einval("unknown option");
+}
+p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
+    if (!ctx || !value) return einval("ctx and value must be non-NULL");
+    if (option == P2S_OPT_SCATTER_SEGMENT_ROWS) {
+        *value = ctx->tc.seg_rows;
+        return P2S_OK;
+    }
+    return einval("unknown option");
+}
+p2s_status p2s_stage_mlp16(p2s_ctx *ctx, int H, int W, const float *alpha, void *beta16, void *stream) {
+    if (!ctx || !alpha || !beta16) return einval("ctx, alpha and beta16 must be non-NULL");
+    if (!(ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16)) {
+        set_error("the 16-bit operand layout exists for FP16 and BF16 contexts only");
+        return P2S_EUNSUPPORTED;
+    }
+    FieldGeom g;
+    p2s_status st = geometry(ctx, H, W, &g);
+    if (st != P2S_OK) return st;
+    return launch_net16(ctx, g, 1, alpha, beta16, 1, ctx->d_status, (cudaStream_t)stream);
+}
 
 p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, const p2s_image *out, void *stream) {
     if (!ctx || !beta) return einval("ctx and beta must be non-NULL");
@@ -515,6 +544,15 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
     if (xw->data == out->data) return einval("out must not alias xw");
     const float *ip[1] = {xw->data};
     float *op[1] = {out->data};
+    if ((ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) && ctx->form == P2S_SCATTER) {
+        cudaStream_t s = (cudaStream_t)stream;
+        void *b16 = nullptr;
+        P2S_CUDA(cudaMallocAsync(&b16, beta16_bytes(xw->H, xw->W, 1), s));
+        st = launch_pack16(ctx, xw->H, xw->W, 1, beta, b16, s);
+        if (st == P2S_OK) st = launch_scatter_tc(ctx, xw->H, xw->W, xw->C, 1, ip, op, b16, ctx->d_status, s);
+        cudaFreeAsync(b16, s);
+        return st;
+    }
     if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) {
         FieldGeom g;
         if ((st = geometry(ctx, xw->H, xw->W, &g)) != P2S_OK) return st;
@@ -536,8 +574,10 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
     const bool tc = ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16;
     // bound the FP32 path's beta scratch to ~1 GiB per launch group
     int chunk = kMaxBatch;
-    const size_t beta_px = tc ? 0 : npx * ctx->K * sizeof(float);
-    while (chunk > 1 && (size_t)chunk * beta_px > (1ull << 30)) chunk /= 2;
+    const bool tc_scatter = tc && ctx->form == P2S_SCATTER;
+    const size_t beta_px = tc_scatter ? beta16_bytes(H, W, 1) : tc ? 0 : npx * ctx->K * sizeof(float);
+    const size_t beta_cap = tc_scatter ? (4ull << 30) : (1ull << 30);
+    while (chunk > 1 && (size_t)chunk * beta_px > beta_cap) chunk /= 2;
     for (int i0 = 0; i0 < n; i0 += chunk) {
         const int nb = n - i0 < chunk ? n - i0 : chunk;
         FrameBatch fb;
@@ -571,7 +611,10 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
         }
         st = launch_fields(ctx, g, fb, alpha, fscr, s);
         if (st == P2S_OK) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
-        if (tc) {
+        if (tc && ctx->form == P2S_SCATTER) {
+            if (st == P2S_OK) st = launch_net16(ctx, g, nb, alpha, beta, 1, ctx->d_status, s);
+            if (st == P2S_OK) st = launch_scatter_tc(ctx, H, W, C, nb, xwp, op, beta, ctx->d_status, s);
+        } else if (tc) {
             if (st == P2S_OK) st = launch_tc(ctx, kTcFull, g, nb, C, xwp, op, alpha, nullptr, nullptr, ctx->d_status, s);
         } else {
             if (st == P2S_OK) st = launch_mlp_simt(ctx, g, nb, alpha, beta, s);

@@ -58,6 +58,14 @@ struct TcPack {
     size_t W_bytes = 0, H_bytes = 0;
     int n_mlp = 0, h1p = 0, h2p = 0, n3 = 0, fmt = 0, split = 0;
     int ready = 0;
+    void *d_Hs = nullptr;  // basis for the scatter kernel, tap-column-major [14][1104][8] 16-bit
+    int seg_rows = 0;      // source rows per scatter work unit (0: default)
+};
+
+// One B image of the tensor-core weight stream: byte offset and size in the
+// stream, N rows, K depth (canonical no-swizzle K-major layout).
+struct Item16 {
+    uint32_t offset, bytes, n, k;
 };
 
 }  // namespace p2s
@@ -146,5 +154,17 @@ p2s_status launch_tc(p2s_ctx *ctx, int mode, const FieldGeom &g, int n, int C, c
                      float *const *y, const float *alpha, const float *beta_in, float *beta_out, int *status,
                      cudaStream_t st);
 constexpr int kTcFull = 0, kTcMlpOnly = 1, kTcBlurOnly = 2;
+
+// Network kernel: beta of n frames into the 16-bit operand layout
+// [frame][row][14][col][8]; `ones` sets entries K, K + 1 (folded bias).
+size_t beta16_bytes(int H, int W, int n);
+p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones,
+                        int *status, cudaStream_t st);
+// FP32 beta [n][H][W][K] -> the 16-bit layout (entries k >= K zero).
+p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, void *beta16, cudaStream_t st);
+// Tensor-core scatter blur of n frames of one size from the 16-bit beta.
+p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, float *const *y,
+                             const void *beta16, int *status, cudaStream_t st);
+int scatter_segment_rows(const p2s_ctx *ctx, int H);
 
 }  // namespace p2s

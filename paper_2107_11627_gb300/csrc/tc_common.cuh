@@ -1,0 +1,56 @@
+// Helpers shared by the tcgen05 kernels: bounded mbarrier waits with a CTA
+// abort flag, and packing of two FP32 values into a 16-bit operand pair.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "tc_ptx.cuh"
+
+namespace p2s {
+namespace tcc {
+
+// Two FP32 values -> one 32-bit word of FP16 (fmt 0) or BF16 (fmt 1), RNE.
+__device__ __forceinline__ uint32_t pack2(float a, float b, int fmt) {
+    if (fmt == 1) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+struct Ctl {
+    volatile int *abort;
+    int *status;
+};
+
+// Bounded wait (about 2 s at 2 GHz); on timeout flags the CTA and the status
+// word.  Once the CTA is flagged every wait returns false at once, so all
+// roles run their (data-independent) loops to the end and meet at teardown.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Ctl &ctl, int code) {
+    if (ptx::mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (int spins = 0;; ++spins) {
+        if (ptx::mbar_try(bar, parity)) return true;
+        if (*ctl.abort) return false;
+        if (spins > 4) __nanosleep(spins < 64 ? 32 : 128);  // leave issue slots to working warps
+        if (clock64() - t0 > 4000000000ll) {
+            *ctl.abort = 1;
+            atomicOr(ctl.status, code);
+            return false;
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag: lets issued copies and MMAs land
+// before the CTA's shared and tensor memory are released.
+__device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!ptx::mbar_try(bar, parity) && clock64() - t0 < 4000000000ll) {
+    }
+}
+
+}  // namespace tcc
+}  // namespace p2s

@@ -65,6 +65,9 @@ _SIGS = {
                                    C.POINTER(C.c_ulonglong), C.c_void_p, C.c_void_p]),
     "p2s_stage_warp": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
     "p2s_stage_mlp": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "p2s_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "p2s_get_option": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "p2s_stage_mlp16": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_stage_blur": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
     "p2s_stage_mlp_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_noll_covariance": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
@@ -266,6 +269,24 @@ class Simulator:
         out = torch.empty((H, W, self.K), dtype=torch.float32, device="cuda")
         _check(lib().p2s_stage_mlp(self.ctx, H, W, C.c_void_p(alpha.data_ptr()), C.c_void_p(out.data_ptr()),
                                    _stream_handle(stream)), "p2s_stage_mlp")
+        return out
+
+    OPTIONS = {"scatter_segment_rows": 1}
+
+    def set_option(self, name: str, value: int):
+        _check(lib().p2s_set_option(self.ctx, self.OPTIONS[name], int(value)), "p2s_set_option")
+
+    def get_option(self, name: str) -> int:
+        v = C.c_int(0)
+        _check(lib().p2s_get_option(self.ctx, self.OPTIONS[name], C.byref(v)), "p2s_get_option")
+        return v.value
+
+    def stage_mlp16(self, H: int, W: int, alpha, stream=None):
+        """beta in the 16-bit operand layout [H][14][W][8] (int16 tensor holding FP16/BF16 bits)."""
+        torch = _torch()
+        out = torch.empty((H, 14, W, 8), dtype=torch.int16, device="cuda")
+        _check(lib().p2s_stage_mlp16(self.ctx, H, W, C.c_void_p(alpha.data_ptr()), C.c_void_p(out.data_ptr()),
+                                     _stream_handle(stream)), "p2s_stage_mlp16")
         return out
 
     def stage_blur(self, xw, beta, stream=None):

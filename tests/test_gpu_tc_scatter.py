@@ -1,0 +1,149 @@
+"""GPU parity of the tensor-core scatter path (y = sum_k h_k * (beta_k . x_w),
+Sec. 3.1): the network kernel's 16-bit operand layout, the shifted-operand
+scatter blur, and whole frames, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.fields import CorrParams
+from oracle.precision import bf16
+from paper_2107_11627_gb300 import inputs
+
+from gpu_common import TOL_BF16, cfg2, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _sim(prec, s=8, seg=None):
+    from paper_2107_11627_gb300 import p2s
+
+    c = cfg2()
+    sim = p2s.Simulator(c["H"], c["taps"], c["layers"], anchor_spacing=s, corr_len_px=(16.0,), precision=prec,
+                        form="scatter")
+    if seg is not None:
+        sim.set_option("scatter_segment_rows", seg)
+    return sim
+
+
+def _alpha_f32(seed, dr, h, w, s=8):
+    a = oracle.fields.alpha_anchors(seed, dr, h, w, CorrParams(s, (16.0,))).astype(np.float32)
+    full = np.zeros(a.shape[:2] + (36,), dtype=np.float32)
+    full[..., 1:] = a
+    return full
+
+
+def _decode16(t, prec):
+    """[H][14][W][8] 16-bit words -> float64 [H][W][112]."""
+    u = t.cpu().numpy().view(np.uint16)
+    if prec == "fp16":
+        v = u.view(np.float16).astype(np.float64)
+    else:
+        v = (u.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    h, g, w, e = v.shape
+    return v.transpose(0, 2, 1, 3).reshape(h, w, g * e)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("h,w", [(64, 128), (37, 150), (2, 3)])
+def test_network_operand_layout(prec, h, w):
+    """beta without the last bias in k < K, exactly 1 at K, K+1 (bias fold), exactly 0 beyond.
+    Bound: FP16 storage keeps the 2e-3 budget; BF16 storage alone rounds each entry by up to
+    2^-9 relative (RNE, 8 significand bits), so its bound is 4e-3."""
+    sim = _sim(prec)
+    al = _alpha_f32(21, 4.0, h, w)
+    b16 = sim.stage_mlp16(h, w, torch.from_numpy(al).cuda())
+    sim.check()
+    v = _decode16(b16, prec)
+    layers = cfg2()["layers"]
+    ap = oracle.fields.alpha_pixels(al[..., 1:].astype(np.float64), h, w, 8)
+    ref = oracle.mlp.forward(ap[..., 2:], layers) - layers[-1][1]
+    tol = TOL_BF16 if prec == "fp16" else 4e-3
+    assert rel(v[..., :100], ref) < tol, rel(v[..., :100], ref)
+    assert np.all(v[..., 100:102] == 1.0)
+    assert np.all(v[..., 102:] == 0.0)
+
+
+@pytest.mark.parametrize("c", [3, 1])
+@pytest.mark.parametrize("h,w", [(40, 130), (33, 64), (1, 1), (70, 300), (300, 150)])
+def test_blur_stage_fp16(c, h, w):
+    sim = _sim("fp16")
+    rng = np.random.default_rng(31)
+    xw = inputs.blob_image(h, w, c, 1003)
+    beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
+    y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda())
+    sim.check()
+    y = y.cpu().numpy()
+    ref = oracle.blur.scatter(xw.astype(np.float64), beta.astype(np.float64), cfg2()["H"], 33, 33)
+    assert rel(y, ref) < TOL_BF16, rel(y, ref)
+
+
+@pytest.mark.parametrize("seg", [2, 6, 34, 128])
+def test_blur_stage_segments(seg):
+    """Work units of `seg` source rows: boundary rows summed across units must equal one pass."""
+    sim = _sim("fp16", seg=seg)
+    assert sim.get_option("scatter_segment_rows") == seg
+    rng = np.random.default_rng(33)
+    h, w = 90, 140
+    xw = inputs.blob_image(h, w, 3, 1005)
+    beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
+    y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
+    sim.check()
+    ref = oracle.blur.scatter(xw.astype(np.float64), beta.astype(np.float64), cfg2()["H"], 33, 33)
+    assert rel(y, ref) < TOL_BF16, rel(y, ref)
+
+
+def test_blur_stage_bf16_rounding_points():
+    """BF16 operands: only beta and H are rounded to BF16 (checked against the
+    oracle with those two tensors rounded), everything else FP32."""
+    sim = _sim("bf16")
+    rng = np.random.default_rng(32)
+    h, w = 48, 160
+    xw = inputs.blob_image(h, w, 3, 1004)
+    beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
+    y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
+    emu = oracle.blur.scatter(xw.astype(np.float64), bf16(beta), bf16(cfg2()["H"]), 33, 33)
+    assert rel(y, emu) < 2e-5, rel(y, emu)
+
+
+@pytest.mark.parametrize("s", [8, 1])
+def test_frames_fp16(s):
+    sim = _sim("fp16", s=s)
+    shapes = [(96, 80), (50, 200), (96, 80)]
+    xs = [inputs.blob_image(h, w, 3, 1000 + i) for i, (h, w) in enumerate(shapes)]
+    dr, seeds = [1.5, 4.0, 6.0], [10**6, 10**6 + 1, 10**6 + 2]
+    ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
+    sim.check()
+    for i in range(3):
+        ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
+                                    CorrParams(s, (16.0,)), (33, 33), form="scatter")
+        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_BF16, (i, rel(ys[i].cpu().numpy(), ref.y))
+
+
+def test_full_size_frame_fp16():
+    """One 512 x 512 RGB frame of the benchmark workload (several segments), whole frame checked."""
+    sim = _sim("fp16")
+    x = inputs.blob_image(512, 512, 3, 1000)
+    (y,) = sim.simulate([torch.from_numpy(x).cuda()], [3.0], [10**6])
+    sim.check()
+    ref = oracle.frame.simulate(x.astype(np.float64), 10**6, 3.0, cfg2()["H"], cfg2()["layers"],
+                                CorrParams(8, (16.0,)), (33, 33), form="scatter")
+    assert rel(y.cpu().numpy(), ref.y) < TOL_BF16
+
+
+def test_batch_invariance_fp16():
+    """A frame's result does not depend on the batch it is simulated in (atomic summation
+    order aside): alone vs. third of three."""
+    sim = _sim("fp16")
+    xs = [inputs.blob_image(160, 200, 3, 1010 + i) for i in range(3)]
+    ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], [2.0, 3.0, 4.0], [7, 8, 9])
+    (alone,) = sim.simulate([torch.from_numpy(xs[2]).cuda()], [4.0], [9])
+    sim.check()
+    assert rel(ys[2].cpu().numpy(), alone.cpu().numpy()) < 1e-6
