@@ -199,8 +199,22 @@ p2s_status p2s_check(p2s_ctx *ctx, void *stream);
  * depend on them beyond floating-point summation order):
  *   P2S_OPT_SCATTER_SEGMENT_ROWS  source rows per work unit of the
  *       tensor-core scatter blur (even, >= 2; 0 = default 128).  Target rows
- *       within 16 rows of a segment boundary are summed with atomic adds. */
-typedef enum { P2S_OPT_SCATTER_SEGMENT_ROWS = 1 } p2s_option;
+ *       within 16 rows of a segment boundary are summed with atomic adds.
+ *   P2S_OPT_GRAPHS  1: p2s_simulate captures its launches into a CUDA graph,
+ *       instantiated once per batch signature (the frames' sizes and channel
+ *       counts, in order) and afterwards only updated with each call's
+ *       pointers, seeds and strengths.  Scratch then comes from an arena owned
+ *       by the context (grown on demand, which synchronises once), so calls of
+ *       one context must not overlap on the GPU in this mode.  Ignored while
+ *       profiling.  0 (default): plain launches.
+ *   P2S_OPT_GRAPH_INSTANTIATIONS, P2S_OPT_GRAPH_UPDATES  (read only) how many
+ *       graphs were instantiated / updated in place so far. */
+typedef enum {
+    P2S_OPT_SCATTER_SEGMENT_ROWS = 1,
+    P2S_OPT_GRAPHS = 2,
+    P2S_OPT_GRAPH_INSTANTIATIONS = 3,
+    P2S_OPT_GRAPH_UPDATES = 4
+} p2s_option;
 p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value);
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value);
 

@@ -39,6 +39,9 @@ constexpr int kK1 = 48;                    // layer-1 depth: 33 modes padded
 constexpr int kGroups = 14;                // beta16 k-groups of 8 (K padded to 112)
 constexpr int kA1Bytes = kTile * kK1 * 2;  // [6 k-groups][128 rows][16 B]
 constexpr int kMaxItems = 6;
+constexpr int kMaxAx = kTile + 1;           // anchor columns a 128-pixel unit touches (spacing 1)
+constexpr int kRowBytes = (kMaxAx * kHiModes * 4 + 127) & ~127;  // interpolated anchor row, per group
+static_assert(kRowBytes % 128 == 0 && kA1Bytes % 1024 == 0, "shared-memory offsets stay 16-byte aligned");
 
 struct Params {
     const float *alpha;
@@ -65,7 +68,8 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = ptx::smem_u32(sm);
     const uint32_t offA1 = (p.wbytes + 1023) & ~1023u;
-    const uint32_t offBias = offA1 + 2 * kA1Bytes;
+    const uint32_t offRow = offA1 + 2 * kA1Bytes;
+    const uint32_t offBias = offRow + 2 * kRowBytes;
     const uint32_t offBar = offBias + (uint32_t)(p.h1p + p.h2p) * 4;
     const uint32_t offMisc = offBar + kNBar * 8;
     float *sbias = (float *)(sm + offBias);
@@ -166,24 +170,32 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
             const int row = rem / p.tiles_x;
             const int col = (rem - row * p.tiles_x) * kTile + m;
             bool ok = true;
-            // ---- layer-1 operand: alpha_4..36 at (row, col), bilinear from the anchors ----
+            // ---- layer-1 operand: alpha_4..36 at (row, col), bilinear from the anchors.
+            //      The group first interpolates the two anchor rows at this image row
+            //      (shared by all 128 pixels), then each pixel interpolates along x. ----
             {
-                const int gj = min(col, p.W - 1);
-                const int ay = row / p.s, ax = gj / p.s;
-                const float fy = (float)(row - ay * p.s) * p.inv_s, fx = (float)(gj - ax * p.s) * p.inv_s;
-                const float *a = p.alpha + ((size_t)f * p.Ah * p.Aw + (size_t)ay * p.Aw + ax) * kAlphaStride;
+                float *arow = (float *)(sm + offRow + grp * kRowBytes);
+                const int c0 = col - m;
+                const int ay = row / p.s;
+                const float fy = (float)(row - ay * p.s) * p.inv_s;
+                const int ax0 = min(c0, p.W - 1) / p.s;
+                const int nax = min(min(c0 + kTile - 1, p.W - 1) / p.s + 2, p.Aw) - ax0;
+                const float *a = p.alpha + ((size_t)f * p.Ah * p.Aw + (size_t)ay * p.Aw + ax0) * kAlphaStride;
                 const float *b = a + (size_t)p.Aw * kAlphaStride;
+                for (int e = m; e < nax * kHiModes; e += kTile) {
+                    const int ax = e / kHiModes, k = e - ax * kHiModes;
+                    const int off = ax * kAlphaStride + k + 3;
+                    arow[e] = (1.0f - fy) * __ldg(a + off) + fy * __ldg(b + off);
+                }
+                ptx::named_bar(2 + grp, kTile);
+                const int gj = min(col, p.W - 1);
+                const int ax = gj / p.s - ax0;
+                const float fx = (float)(gj - (ax + ax0) * p.s) * p.inv_s;
+                const float *r0p = arow + ax * kHiModes;
+                const float *r1p = r0p + (ax + 1 < nax ? kHiModes : 0);
                 float v[kK1];
 #pragma unroll
-                for (int k = 0; k < kK1; ++k) {
-                    if (k < kHiModes) {
-                        const int sl = k + 3;
-                        v[k] = (1.0f - fy) * ((1.0f - fx) * __ldg(a + sl) + fx * __ldg(a + kAlphaStride + sl)) +
-                               fy * ((1.0f - fx) * __ldg(b + sl) + fx * __ldg(b + kAlphaStride + sl));
-                    } else {
-                        v[k] = 0.f;
-                    }
-                }
+                for (int k = 0; k < kK1; ++k) v[k] = k < kHiModes ? (1.0f - fx) * r0p[k] + fx * r1p[k] : 0.f;
 #pragma unroll
                 for (int g = 0; g < kK1 / 8; ++g) {
                     uint4 u;
@@ -195,7 +207,8 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                 }
                 ptx::fence_proxy_async();
                 ptx::fence_before();
-                __syncwarp();
+                // every pixel has read the anchor row before the group's next unit rewrites it
+                ptx::named_bar(2 + grp, kTile);
                 if (lane == 0) ptx::mbar_arrive(BAR(kA1 + grp));
             }
             // ---- layers 1, 2: D -> bias, ReLU -> packed activations in place ----
@@ -208,21 +221,38 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
             for (int L = 0; L < 2; ++L) {
                 ok = __all_sync(0xffffffffu, wait_bar(BAR(done[L] + grp), ph, ctl, 4) && ok);
                 ptx::fence_after();
-                for (int q = 0; ok && q < width[L] / 32; ++q) {
-                    uint32_t d[32];
-                    ptx::tmem_ld32(dreg[L] + 32 * q, d);
-                    ptx::tmem_wait_ld();
-                    uint32_t u[16];
+                if (ok) {
+                    // TMEM loads double-buffered: chunk q + 1 is in flight while q converts
+                    const int nq = width[L] / 32;
+                    uint32_t d[2][32];
+                    ptx::tmem_ld32(dreg[L], d[0]);
+#pragma unroll 1
+                    for (int q = 0; q < nq; q += 2) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float h0 = fmaxf(__uint_as_float(d[2 * j]) + sbias[boff[L] + 32 * q + 2 * j], 0.f);
-                        const float h1 = fmaxf(__uint_as_float(d[2 * j + 1]) + sbias[boff[L] + 32 * q + 2 * j + 1], 0.f);
-                        u[j] = pack2(h0, h1, p.ab_fmt);
+                        for (int h = 0; h < 2; ++h) {
+                            const int qq = q + h;
+                            if (qq < nq) {
+                                ptx::tmem_wait_ld_dep(d[h]);
+                                if (qq + 1 < nq) ptx::tmem_ld32(dreg[L] + 32 * (qq + 1), d[h ^ 1]);
+                                const float4 *bv = (const float4 *)(sbias + boff[L] + 32 * qq);
+                                uint32_t u[16];
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    const float4 bb = bv[j];
+                                    const float h0 = fmaxf(__uint_as_float(d[h][4 * j]) + bb.x, 0.f);
+                                    const float h1 = fmaxf(__uint_as_float(d[h][4 * j + 1]) + bb.y, 0.f);
+                                    const float h2 = fmaxf(__uint_as_float(d[h][4 * j + 2]) + bb.z, 0.f);
+                                    const float h3 = fmaxf(__uint_as_float(d[h][4 * j + 3]) + bb.w, 0.f);
+                                    u[2 * j] = pack2(h0, h1, p.ab_fmt);
+                                    u[2 * j + 1] = pack2(h2, h3, p.ab_fmt);
+                                }
+                                const uint32_t(&u0)[8] = *reinterpret_cast<const uint32_t(*)[8]>(&u[0]);
+                                const uint32_t(&u1)[8] = *reinterpret_cast<const uint32_t(*)[8]>(&u[8]);
+                                ptx::tmem_st8(dreg[L] + 16 * qq, u0);
+                                ptx::tmem_st8(dreg[L] + 16 * qq + 8, u1);
+                            }
+                        }
                     }
-                    const uint32_t(&u0)[8] = *reinterpret_cast<const uint32_t(*)[8]>(&u[0]);
-                    const uint32_t(&u1)[8] = *reinterpret_cast<const uint32_t(*)[8]>(&u[8]);
-                    ptx::tmem_st8(dreg[L] + 16 * q, u0);
-                    ptx::tmem_st8(dreg[L] + 16 * q + 8, u1);
                 }
                 ptx::tmem_wait_st();
                 ptx::fence_before();
@@ -234,31 +264,40 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
             ptx::fence_after();
             const bool store = ok && f < p.n && col < p.W;
             uint4 *dst = p.beta16 + ((size_t)(f * p.H + row) * kGroups) * p.W + col;
+            uint32_t d[2][16];
+            if (ok) ptx::tmem_ld16(r0, d[0]);
 #pragma unroll 1
-            for (int q = 0; q < kGroups / 2; ++q) {
-                uint32_t d[16];
-                if (ok && 16 * q < p.n3) {
-                    ptx::tmem_ld16(r0 + 16 * q, d);
-                    ptx::tmem_wait_ld();
-                }
-                float v[16];
+            for (int q = 0; q < kGroups / 2; q += 2) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int k = 16 * q + j;
-                    v[j] = k < p.K ? __uint_as_float(d[j]) : ((p.ones && (k == p.K || k == p.K + 1)) ? 1.0f : 0.0f);
-                }
-                if (store) {
+                for (int h = 0; h < 2; ++h) {
+                    const int qq = q + h;
+                    if (qq < kGroups / 2) {
+                        if (ok) {
+                            ptx::tmem_wait_ld_dep(d[h]);
+                            if (qq + 1 < kGroups / 2 && 16 * (qq + 1) < p.n3) ptx::tmem_ld16(r0 + 16 * (qq + 1), d[h ^ 1]);
+                        }
+                        float v[16];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        uint4 u;
-                        u.x = pack2(v[8 * h + 0], v[8 * h + 1], p.ab_fmt);
-                        u.y = pack2(v[8 * h + 2], v[8 * h + 3], p.ab_fmt);
-                        u.z = pack2(v[8 * h + 4], v[8 * h + 5], p.ab_fmt);
-                        u.w = pack2(v[8 * h + 6], v[8 * h + 7], p.ab_fmt);
-                        dst[(size_t)(2 * q + h) * p.W] = u;
+                        for (int j = 0; j < 16; ++j) {
+                            const int k = 16 * qq + j;
+                            v[j] = k < p.K ? __uint_as_float(d[h][j])
+                                           : ((p.ones && (k == p.K || k == p.K + 1)) ? 1.0f : 0.0f);
+                        }
+                        if (store) {
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                uint4 u;
+                                u.x = pack2(v[8 * e + 0], v[8 * e + 1], p.ab_fmt);
+                                u.y = pack2(v[8 * e + 2], v[8 * e + 3], p.ab_fmt);
+                                u.z = pack2(v[8 * e + 4], v[8 * e + 5], p.ab_fmt);
+                                u.w = pack2(v[8 * e + 6], v[8 * e + 7], p.ab_fmt);
+                                dst[(size_t)(2 * qq + e) * p.W] = u;
+                            }
+                        }
                     }
                 }
             }
+            if (ok) ptx::tmem_wait_ld();
             // D3 fully read before this slot's next layer-1 result lands in r0
             ptx::fence_before();
         }
@@ -306,7 +345,7 @@ int net_smem_bytes(const p2s_ctx *ctx) {
     const Item16 *it = (const Item16 *)ctx->tc_items.data();
     for (int i = 0; i < ctx->tc.n_mlp; ++i) w += it[i].bytes;
     const uint32_t offA1 = (w + 1023) & ~1023u;
-    return (int)(offA1 + 2 * kA1Bytes + (ctx->tc.h1p + ctx->tc.h2p) * 4 + kNBar * 8 + 16 + 1024);
+    return (int)(offA1 + 2 * kA1Bytes + 2 * kRowBytes + (ctx->tc.h1p + ctx->tc.h2p) * 4 + kNBar * 8 + 16 + 1024);
 }
 
 p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones,

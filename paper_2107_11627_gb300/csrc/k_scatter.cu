@@ -471,7 +471,7 @@ using namespace sc;
 // The basis, tap-column-major: row r = tx * 33 + ty (r < 1089, then 15 zero
 // rows), 16-bit groups of 8 along k: [14][1104][8]; rows K and K + 1 carry the
 // folded bias PSF h_b = sum_k b3_k H_k as an exact hi/lo pair.
-static p2s_status scatter_prepare(p2s_ctx *ctx) {
+p2s_status scatter_prepare(p2s_ctx *ctx) {
     if (ctx->tc.d_Hs) return P2S_OK;
     p2s_status s0 = tc_prepare(ctx);
     if (s0 != P2S_OK) return s0;

@@ -65,20 +65,19 @@ struct Item {
 };
 
 struct Params {
-    const float *xw[kMaxBatch];
-    float *y[kMaxBatch];
-    const float *alpha;
+    TcFrame fr[kMaxTcFrames];  // per-frame pointers and geometry; tiles numbered frame by frame
+    int n_frames;
     const float *beta_in;
     float *beta_out;
     const uint8_t *stream;
     const float *bias;  // b1 [h1p], b2 [h2p]
     const float *b3;    // [K]
     int *status;
-    int n, H, W, C, s, Ah, Aw;
+    int C, s;
     float inv_s;
     int K, h1p, h2p, n3;
     int mode, fold, ab_fmt, split;
-    int tiles_x, tiles_y, tiles_total;
+    int tiles_total;
     int n_mlp_items;
     Item item[6 + kChunks];  // network items (hi[,lo] per layer), then chunks
 };
@@ -100,6 +99,21 @@ using tcc::Ctl;
 using tcc::drain_bar;
 using tcc::pack2;
 using tcc::wait_bar;
+
+static_assert(sizeof(Params) <= 32000, "kernel parameter block (frame table) exceeds the 32 KB limit");
+
+// frame of a global tile index (frames are laid out one after another)
+__device__ __forceinline__ int frame_of(const Params &p, int tile) {
+    int lo = 0, hi = p.n_frames - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.fr[mid].tile_base <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
 template <int C>
 __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constant__ Params p) {
@@ -148,8 +162,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
     const int items_per_pair = (do_mlp ? p.n_mlp_items : 0) + (do_blur ? kChunks : 0);
 
     auto n_pairs_of = [&](int tile) {
-        const int ty = (tile % (p.tiles_x * p.tiles_y)) / p.tiles_x;
-        const int rows = min(kBand, p.H - ty * kBand);
+        const TcFrame &F = p.fr[frame_of(p, tile)];
+        const int ty = (tile - F.tile_base) / F.tiles_x;
+        const int rows = min(kBand, F.H - ty * kBand);
         return (rows + 1) >> 1;
     };
 
@@ -263,20 +278,21 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
         const int tid_e = threadIdx.x - 64;    // 0..255
         uint32_t pairs = 0, uses = 0;
         for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
-            const int per_frame = p.tiles_x * p.tiles_y;
-            const int frame = tile / per_frame;
-            const int ty = (tile % per_frame) / p.tiles_x, tx = tile % p.tiles_x;
+            const int frame = frame_of(p, tile);
+            const TcFrame &F = p.fr[frame];
+            const int lt = tile - F.tile_base;
+            const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
             const int r_band = ty * kBand, c0 = tx * kStrip;
             const int npair = n_pairs_of(tile);
             if (do_blur) {
                 ptx::named_bar(1, kEpi);  // previous tile fully consumed
-                const float *x = p.xw[frame];
+                const float *x = F.xw;
                 for (int i = tid_e; i < kTR * kTC; i += kEpi) {
                     const int tr = i / kTC, tcol = i - tr * kTC;
                     const int gr = r_band - kHalo + tr, gc = c0 - kHalo + tcol;
                     float r = 0.f, g = 0.f, b = 0.f;
-                    if (gr >= 0 && gr < p.H && gc >= 0 && gc < p.W) {
-                        const float *px = x + ((size_t)gr * p.W + gc) * C;
+                    if (gr >= 0 && gr < F.H && gc >= 0 && gc < F.W) {
+                        const float *px = x + ((size_t)gr * F.W + gc) * C;
                         r = __ldg(px);
                         if (C == 3) {
                             g = __ldg(px + 1);
@@ -292,15 +308,15 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                 const uint32_t ph = pairs & 1;
                 bool ok = true;
                 const int row = r_band + 2 * rp + half;  // this half's row for network stages
-                const bool col_ok = c0 + col < p.W, row_ok = row < p.H;
+                const bool col_ok = c0 + col < F.W, row_ok = row < F.H;
                 if (do_mlp) {
                     // ---- network input: alpha_4..36 at (row, col), bilinear from the anchors ----
                     {
-                        const int gi = min(row, p.H - 1), gj = min(c0 + col, p.W - 1);
+                        const int gi = min(row, F.H - 1), gj = min(c0 + col, F.W - 1);
                         const int ay = gi / p.s, ax = gj / p.s;
                         const float fy = (float)(gi - ay * p.s) * p.inv_s, fx = (float)(gj - ax * p.s) * p.inv_s;
-                        const float *a = p.alpha + ((size_t)frame * p.Ah * p.Aw + (size_t)ay * p.Aw + ax) * kAlphaStride;
-                        const float *b = a + (size_t)p.Aw * kAlphaStride;
+                        const float *a = F.alpha + ((size_t)ay * F.Aw + ax) * kAlphaStride;
+                        const float *b = a + (size_t)F.Aw * kAlphaStride;
                         float v[48];
 #pragma unroll
                         for (int m = 0; m < 48; ++m) {
@@ -374,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                         }
                         if (p.mode == kMlpOnly) {
                             if (row_ok && col_ok) {
-                                float *o = p.beta_out + (((size_t)frame * p.H + row) * p.W + c0 + col) * p.K;
+                                float *o = p.beta_out + ((size_t)row * F.W + c0 + col) * p.K;
 #pragma unroll
                                 for (int k = 0; k < kKP; ++k)
                                     if (k < p.K) o[k] = v[k] + __ldg(p.b3 + k);
@@ -398,8 +414,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                     if (lane == 0) ptx::mbar_arrive(BAR(kBetab));
                 } else {
                     // blur alone: beta of (row, col) from global, no bias fold
-                    const int gi = min(row, p.H - 1), gj = min(c0 + col, p.W - 1);
-                    const float *bp = p.beta_in + (((size_t)frame * p.H + gi) * p.W + gj) * p.K;
+                    const int gi = min(row, F.H - 1), gj = min(c0 + col, F.W - 1);
+                    const float *bp = p.beta_in + ((size_t)gi * F.W + gj) * p.K;
                     for (int q = 0; q < kKP / 16; ++q) {
                         uint32_t u[8];
 #pragma unroll
@@ -519,8 +535,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const int orow = r_band + 2 * rp + i;
-                        if (orow < p.H && col_ok) {
-                            float *o = p.y[frame] + ((size_t)orow * p.W + c0 + col) * C;
+                        if (orow < F.H && col_ok) {
+                            float *o = F.y + ((size_t)orow * F.W + c0 + col) * C;
 #pragma unroll
                             for (int ch = 0; ch < C; ++ch) o[ch] = acc[i][ch] + xchg[col * 6 + i * 3 + ch];
                         }
@@ -664,33 +680,51 @@ p2s_status tc_prepare(p2s_ctx *ctx) {
 
 int tc_smem_bytes() { return kSmemBytes; }
 
-p2s_status launch_tc(p2s_ctx *ctx, int mode, const FieldGeom &g, int n, int C, const float *const *xw,
-                     float *const *y, const float *alpha, const float *beta_in, float *beta_out, int *status,
-                     cudaStream_t st) {
+static p2s_status launch_tc_chunk(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
+                                  float *beta_out, int *status, cudaStream_t st);
+
+p2s_status launch_tc(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
+                     float *beta_out, int *status, cudaStream_t st) {
     if (n <= 0) return P2S_OK;
+    if ((mode != kTcFull) && n != 1) {
+        set_error("the network-only and blur-only tensor-core stages take one frame");
+        return P2S_EINVAL;
+    }
     p2s_status s0 = tc_prepare(ctx);
     if (s0 != P2S_OK) return s0;
-    Params p;
-    std::memset(&p, 0, sizeof p);
-    for (int i = 0; i < n; ++i) {
-        p.xw[i] = xw ? xw[i] : nullptr;
-        p.y[i] = y ? y[i] : nullptr;
+    for (int i0 = 0; i0 < n; i0 += kMaxTcFrames) {
+        const int nb = n - i0 < kMaxTcFrames ? n - i0 : kMaxTcFrames;
+        s0 = launch_tc_chunk(ctx, mode, frames + i0, nb, C, beta_in, beta_out, status, st);
+        if (s0 != P2S_OK) return s0;
     }
-    p.alpha = alpha;
+    return P2S_OK;
+}
+
+static p2s_status launch_tc_chunk(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
+                                  float *beta_out, int *status, cudaStream_t st) {
+    thread_local Params p;  // large (frame table); copied into the launch by value
+    std::memset(&p, 0, sizeof p);
+    int tiles = 0;
+    double npx = 0.0;
+    for (int i = 0; i < n; ++i) {
+        TcFrame f = frames[i];
+        f.tiles_x = (f.W + kStrip - 1) / kStrip;
+        f.tiles_y = (f.H + kBand - 1) / kBand;
+        f.tile_base = tiles;
+        tiles += f.tiles_x * f.tiles_y;
+        npx += (double)f.H * f.W;
+        p.fr[i] = f;
+    }
+    p.n_frames = n;
     p.beta_in = beta_in;
     p.beta_out = beta_out;
     p.stream = (const uint8_t *)ctx->tc.d_H;
     p.bias = ctx->tc.d_bias;
     p.b3 = ctx->tc.d_bias + ctx->tc.h1p + ctx->tc.h2p;
     p.status = status;
-    p.n = n;
-    p.H = g.H;
-    p.W = g.W;
     p.C = C;
-    p.s = g.s;
-    p.Ah = g.Ah;
-    p.Aw = g.Aw;
-    p.inv_s = 1.0f / (float)g.s;
+    p.s = ctx->s;
+    p.inv_s = 1.0f / (float)ctx->s;
     p.K = ctx->K;
     p.h1p = ctx->tc.h1p;
     p.h2p = ctx->tc.h2p;
@@ -699,15 +733,12 @@ p2s_status launch_tc(p2s_ctx *ctx, int mode, const FieldGeom &g, int n, int C, c
     p.fold = mode == kFull ? 1 : 0;
     p.ab_fmt = ctx->tc.fmt;
     p.split = ctx->tc.split;
-    p.tiles_x = (g.W + kStrip - 1) / kStrip;
-    p.tiles_y = (g.H + kBand - 1) / kBand;
-    p.tiles_total = p.tiles_x * p.tiles_y * n;
+    p.tiles_total = tiles;
     p.n_mlp_items = ctx->tc.n_mlp;
     std::memcpy(p.item, ctx->tc_items.data(), sizeof(p.item));
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const int grid = p.tiles_total < sms ? p.tiles_total : sms;
-    const double npx = (double)g.H * g.W * n;
     double macs_net = 0.0;
     for (int l = 0; l < 3; ++l) macs_net += (double)ctx->dims[l] * ctx->dims[l + 1];
     const double flops = mode == kBlurOnly   ? 2.0 * ctx->K * ctx->T * npx

@@ -1,4 +1,5 @@
 // Host side of libp2s: the C ABI, context set-up in FP64, validation, dispatch.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -355,6 +356,12 @@ void p2s_destroy(p2s_ctx *ctx) {
     cudaFree(ctx->tc.d_H);
     cudaFree(ctx->tc.d_bias);
     cudaFree(ctx->tc.d_Hs);
+    for (auto &kv : ctx->graphs)
+        if (kv.second) cudaGraphExecDestroy(kv.second);
+    cudaFree(ctx->arena);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaEvent_t e : ctx->cap_ev)
+        if (e) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -502,9 +509,10 @@ p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *
     FieldGeom g;
     p2s_status st = geometry(ctx, H, W, &g);
     if (st != P2S_OK) return st;
-    if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16)
-        return launch_tc(ctx, kTcMlpOnly, g, 1, 1, nullptr, nullptr, alpha, nullptr, beta, ctx->d_status,
-                         (cudaStream_t)stream);
+    if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) {
+        const TcFrame f{nullptr, nullptr, alpha, H, W, g.Ah, g.Aw, 0, 0, 0};
+        return launch_tc(ctx, kTcMlpOnly, &f, 1, 1, nullptr, beta, ctx->d_status, (cudaStream_t)stream);
+    }
     return launch_mlp_simt(ctx, g, 1, alpha, beta, (cudaStream_t)stream);
 }
 p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
@@ -514,12 +522,29 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
         ctx->tc.seg_rows = value;
         return P2S_OK;
     }
+    if (option == P2S_OPT_GRAPHS) {
+        if (value != 0 && value != 1) return einval("graphs option is 0 or 1");
+        ctx->use_graphs = value;
+        return P2S_OK;
+    }
     return einval("unknown option");
 }
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
     if (!ctx || !value) return einval("ctx and value must be non-NULL");
     if (option == P2S_OPT_SCATTER_SEGMENT_ROWS) {
         *value = ctx->tc.seg_rows;
+        return P2S_OK;
+    }
+    if (option == P2S_OPT_GRAPHS) {
+        *value = ctx->use_graphs;
+        return P2S_OK;
+    }
+    if (option == P2S_OPT_GRAPH_INSTANTIATIONS) {
+        *value = (int)ctx->graph_instantiations;
+        return P2S_OK;
+    }
+    if (option == P2S_OPT_GRAPH_UPDATES) {
+        *value = (int)ctx->graph_updates;
         return P2S_OK;
     }
     return einval("unknown option");
@@ -556,16 +581,61 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
     if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) {
         FieldGeom g;
         if ((st = geometry(ctx, xw->H, xw->W, &g)) != P2S_OK) return st;
-        return launch_tc(ctx, kTcBlurOnly, g, 1, xw->C, ip, op, nullptr, beta, nullptr, ctx->d_status,
-                         (cudaStream_t)stream);
+        const TcFrame f{xw->data, out->data, nullptr, xw->H, xw->W, g.Ah, g.Aw, 0, 0, 0};
+        return launch_tc(ctx, kTcBlurOnly, &f, 1, xw->C, beta, nullptr, ctx->d_status, (cudaStream_t)stream);
     }
     return launch_blur_simt(ctx, xw->H, xw->W, xw->C, 1, ip, beta, op, ctx->form, (cudaStream_t)stream);
 }
 
 // ---- the whole path --------------------------------------------------------
 
+// Per-call device scratch: stream-ordered allocations, or (graph capture)
+// slices of the context's arena.  In arena mode a request that does not fit
+// is counted in `needed` and served from the arena base so that the capture
+// can finish; the caller then grows the arena and captures again.
+struct Scratch {
+    p2s_ctx *ctx;
+    cudaStream_t s;
+    bool arena;
+    size_t used = 0, needed = 0;
+    bool overflow = false;
+    std::vector<void *> blocks;
+    void *get(size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (arena) {
+            needed = std::max(needed, used + bytes);
+            if (used + bytes > ctx->arena_bytes) {
+                // sizing pass: the capture that gets this address is discarded, never launched
+                overflow = true;
+                used += bytes;
+                return ctx->arena ? ctx->arena : (void *)(uintptr_t)4096;
+            }
+            void *p = (char *)ctx->arena + used;
+            used += bytes;
+            return p;
+        }
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
+        blocks.push_back(p);
+        return p;
+    }
+    size_t mark() const { return used; }
+    // everything obtained after `m` is dead once the stream reaches this point
+    void rewind(size_t m) {
+        if (arena) {
+            used = m;
+        } else {
+            for (void *b : blocks) cudaFreeAsync(b, s);
+            blocks.clear();
+        }
+    }
+    void release() { rewind(0); }
+};
+
+
 static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2s_image *out, const int *idx, int n,
-                                 const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s) {
+                                 const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s,
+                                 Scratch &sc) {
     const int H = frames[idx[0]].H, W = frames[idx[0]].W, C = frames[idx[0]].C;
     FieldGeom g;
     p2s_status st = geometry(ctx, H, W, &g);
@@ -597,8 +667,12 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
         const size_t f_bytes = fields_scratch_bytes(g, nb);
         const size_t xw_bytes = (size_t)nb * npx * C * sizeof(float);
         const size_t b_bytes = (size_t)nb * beta_px;
-        char *scratch = nullptr;
-        P2S_CUDA(cudaMallocAsync((void **)&scratch, a_bytes + f_bytes + xw_bytes + b_bytes + 1024, s));
+        const size_t m0 = sc.mark();
+        char *scratch = (char *)sc.get(a_bytes + f_bytes + xw_bytes + b_bytes + 1024);
+        if (!scratch) {
+            set_error("device allocation failed for per-call scratch");
+            return P2S_ENOMEM;
+        }
         float *alpha = (float *)scratch;
         void *fscr = scratch + ((a_bytes + 255) & ~(size_t)255);
         float *xw = (float *)((char *)fscr + ((f_bytes + 255) & ~(size_t)255));
@@ -614,16 +688,78 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
         if (tc && ctx->form == P2S_SCATTER) {
             if (st == P2S_OK) st = launch_net16(ctx, g, nb, alpha, beta, 1, ctx->d_status, s);
             if (st == P2S_OK) st = launch_scatter_tc(ctx, H, W, C, nb, xwp, op, beta, ctx->d_status, s);
-        } else if (tc) {
-            if (st == P2S_OK) st = launch_tc(ctx, kTcFull, g, nb, C, xwp, op, alpha, nullptr, nullptr, ctx->d_status, s);
         } else {
             if (st == P2S_OK) st = launch_mlp_simt(ctx, g, nb, alpha, beta, s);
             if (st == P2S_OK) st = launch_blur_simt(ctx, H, W, C, nb, xwp, beta, op, ctx->form, s);
         }
-        cudaFreeAsync(scratch, s);
+        sc.rewind(m0);
         if (st != P2S_OK) return st;
     }
     return P2S_OK;
+}
+
+// Tensor-core gather: fields and warp per shape group, then ONE persistent
+// fused launch over every frame of the call (per channel count), whatever
+// their sizes; work is ordered frame by frame, tile by tile.
+static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, const p2s_image *out, int n,
+                                     const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s,
+                                     Scratch &sc) {
+    std::vector<TcFrame> tf[2];  // C = 1, C = 3
+    std::vector<char> done(n, 0);
+    std::vector<int> idx;
+    p2s_status st = P2S_OK;
+    for (int i = 0; i < n && st == P2S_OK; ++i) {
+        if (done[i]) continue;
+        idx.clear();
+        for (int j = i; j < n; ++j)
+            if (!done[j] && same_shape(&frames[i], &frames[j])) {
+                idx.push_back(j);
+                done[j] = 1;
+            }
+        const int H = frames[i].H, W = frames[i].W, C = frames[i].C;
+        FieldGeom g;
+        if ((st = geometry(ctx, H, W, &g)) != P2S_OK) break;
+        const size_t npx = (size_t)H * W;
+        for (size_t i0 = 0; i0 < idx.size() && st == P2S_OK; i0 += kMaxBatch) {
+            const int nb = (int)std::min<size_t>(kMaxBatch, idx.size() - i0);
+            FrameBatch fb;
+            float dr[kMaxBatch];
+            unsigned long long sd[kMaxBatch];
+            const float *ip[kMaxBatch];
+            float *xwm[kMaxBatch];
+            for (int k = 0; k < nb; ++k) {
+                dr[k] = d_over_r0[idx[i0 + k]];
+                sd[k] = seeds[idx[i0 + k]];
+                ip[k] = frames[idx[i0 + k]].data;
+            }
+            fill_batch(&fb, nb, dr, sd);
+            const size_t a_bytes = ((size_t)nb * g.Ah * g.Aw * kAlphaStride * sizeof(float) + 255) & ~(size_t)255;
+            const size_t f_bytes = (fields_scratch_bytes(g, nb) + 255) & ~(size_t)255;
+            const size_t xw_bytes = (size_t)nb * npx * C * sizeof(float);
+            char *buf = (char *)sc.get(a_bytes + f_bytes + xw_bytes);
+            if (!buf) {
+                set_error("device allocation failed for per-call scratch");
+                st = P2S_ENOMEM;
+                break;
+            }
+            float *alpha = (float *)buf;
+            float *xw = (float *)(buf + a_bytes + f_bytes);
+            for (int k = 0; k < nb; ++k) xwm[k] = xw + (size_t)k * npx * C;
+            st = launch_fields(ctx, g, fb, alpha, buf + a_bytes, s);
+            if (st == P2S_OK) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
+            for (int k = 0; k < nb; ++k) {
+                const int f = idx[i0 + k];
+                tf[C == 3 ? 1 : 0].push_back(TcFrame{xwm[k], out[f].data, alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride,
+                                                     H, W, g.Ah, g.Aw, 0, 0, 0});
+            }
+        }
+    }
+    if (st == P2S_OK && !tf[1].empty())
+        st = launch_tc(ctx, kTcFull, tf[1].data(), (int)tf[1].size(), 3, nullptr, nullptr, ctx->d_status, s);
+    if (st == P2S_OK && !tf[0].empty())
+        st = launch_tc(ctx, kTcFull, tf[0].data(), (int)tf[0].size(), 1, nullptr, nullptr, ctx->d_status, s);
+    sc.release();
+    return st;
 }
 
 static p2s_status validate_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
@@ -643,11 +779,10 @@ static p2s_status validate_simulate(p2s_ctx *ctx, const p2s_image *frames, int n
     return P2S_OK;
 }
 
-p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
-                        const unsigned long long *seeds, const p2s_image *out, void *stream) {
-    p2s_status st = validate_simulate(ctx, frames, n, d_over_r0, seeds, out);
-    if (st != P2S_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
+static p2s_status simulate_impl(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                                const unsigned long long *seeds, const p2s_image *out, cudaStream_t s, Scratch &sc) {
+    if ((ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) && ctx->form == P2S_GATHER)
+        return simulate_tc_gather(ctx, frames, out, n, d_over_r0, seeds, s, sc);
     // group frames of one shape, in order of first appearance
     std::vector<char> done(n, 0);
     std::vector<int> idx;
@@ -659,10 +794,122 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
                 idx.push_back(j);
                 done[j] = 1;
             }
-        st = simulate_group(ctx, frames, out, idx.data(), (int)idx.size(), d_over_r0, seeds, s);
+        p2s_status st = simulate_group(ctx, frames, out, idx.data(), (int)idx.size(), d_over_r0, seeds, s, sc);
         if (st != P2S_OK) return st;
     }
     return P2S_OK;
+}
+
+// One-time device preparation that must not happen inside a stream capture.
+static p2s_status prepare_for_capture(p2s_ctx *ctx) {
+    if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) {
+        p2s_status st = tc_prepare(ctx);
+        if (st != P2S_OK) return st;
+        if (ctx->form == P2S_SCATTER && (st = scatter_prepare(ctx)) != P2S_OK) return st;
+    }
+    if (!ctx->cap_stream) {
+        P2S_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        P2S_CUDA(cudaEventCreateWithFlags(&ctx->cap_ev[0], cudaEventDisableTiming));
+        P2S_CUDA(cudaEventCreateWithFlags(&ctx->cap_ev[1], cudaEventDisableTiming));
+    }
+    return P2S_OK;
+}
+
+// p2s_simulate as a CUDA graph: the call's launches are captured on the
+// context's stream (ordered after the caller's stream by an event), the
+// graph is instantiated once per batch signature and later only updated
+// with the new arguments (pointers, seeds, strengths), then launched.
+static p2s_status simulate_graph(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                                 const unsigned long long *seeds, const p2s_image *out, cudaStream_t user) {
+    p2s_status st = prepare_for_capture(ctx);
+    if (st != P2S_OK) return st;
+    // field filter tables of every torus size in the call (built with synchronous copies)
+    for (int i = 0; i < n; ++i) {
+        FieldGeom g;
+        const FilterTable *t;
+        if ((st = geometry(ctx, frames[i].H, frames[i].W, &g)) != P2S_OK) return st;
+        if ((st = filter_table(ctx, g.Fh, &t)) != P2S_OK || (st = filter_table(ctx, g.Fw, &t)) != P2S_OK) return st;
+    }
+    std::string key;
+    for (int i = 0; i < n; ++i) {
+        char b[48];
+        std::snprintf(b, sizeof b, "%dx%dx%d;", frames[i].H, frames[i].W, frames[i].C);
+        key += b;
+    }
+    cudaStream_t s = ctx->cap_stream;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        Scratch sc{ctx, s, true};
+        P2S_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        st = simulate_impl(ctx, frames, n, d_over_r0, seeds, out, s, sc);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st == P2S_OK && ce != cudaSuccess) {
+            set_error("stream capture failed: %s", cudaGetErrorString(ce));
+            st = P2S_ECUDA;
+        }
+        if (st == P2S_OK && sc.overflow) {
+            cudaGraphDestroy(graph);
+            P2S_CUDA(cudaStreamSynchronize(s));
+            cudaFree(ctx->arena);
+            ctx->arena = nullptr;
+            ctx->arena_bytes = 0;
+            const size_t want = sc.needed + sc.needed / 8;
+            if (cudaMalloc(&ctx->arena, want) != cudaSuccess) {
+                set_error("device allocation of %zu bytes failed for the graph arena", want);
+                return P2S_ENOMEM;
+            }
+            ctx->arena_bytes = want;
+            continue;
+        }
+        if (st != P2S_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        cudaGraphExec_t &exec = ctx->graphs[key];
+        bool ok = false;
+        if (exec) {
+            cudaGraphExecUpdateResultInfo info;
+            ok = cudaGraphExecUpdate(exec, graph, &info) == cudaSuccess;
+            if (ok) {
+                ++ctx->graph_updates;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(exec);
+                exec = nullptr;
+            }
+        }
+        if (!ok) {
+            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                exec = nullptr;
+                set_error("graph instantiation failed: %s", cudaGetErrorString(ie));
+                return P2S_ECUDA;
+            }
+            ++ctx->graph_instantiations;
+        }
+        cudaGraphDestroy(graph);
+        P2S_CUDA(cudaEventRecord(ctx->cap_ev[0], user));
+        P2S_CUDA(cudaStreamWaitEvent(s, ctx->cap_ev[0], 0));
+        P2S_CUDA(cudaGraphLaunch(exec, s));
+        P2S_CUDA(cudaEventRecord(ctx->cap_ev[1], s));
+        P2S_CUDA(cudaStreamWaitEvent(user, ctx->cap_ev[1], 0));
+        return P2S_OK;
+    }
+    set_error("graph arena could not be sized");
+    return P2S_ENOMEM;
+}
+
+p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                        const unsigned long long *seeds, const p2s_image *out, void *stream) {
+    p2s_status st = validate_simulate(ctx, frames, n, d_over_r0, seeds, out);
+    if (st != P2S_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->use_graphs && !ctx->profiling && n > 0) return simulate_graph(ctx, frames, n, d_over_r0, seeds, out, s);
+    Scratch sc{ctx, s, false};
+    st = simulate_impl(ctx, frames, n, d_over_r0, seeds, out, s, sc);
+    sc.release();
+    return st;
 }
 
 p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,

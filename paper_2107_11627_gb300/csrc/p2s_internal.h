@@ -107,6 +107,15 @@ struct p2s_ctx {
     // staging for p2s_simulate_host
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    // CUDA graphs of p2s_simulate (P2S_OPT_GRAPHS): scratch arena, internal
+    // capture stream, instantiated graphs by batch signature
+    int use_graphs = 0;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t cap_ev[2] = {nullptr, nullptr};
+    std::map<std::string, cudaGraphExec_t> graphs;
+    long long graph_updates = 0, graph_instantiations = 0;
     // kernel timing
     bool profiling = false;
     std::vector<p2s::ProfRecord> prof;
@@ -150,9 +159,17 @@ p2s_status launch_blur_simt(const p2s_ctx *ctx, int H, int W, int C, int n, cons
 
 // tensor-core path (k_tc.cu)
 p2s_status tc_prepare(p2s_ctx *ctx);
-p2s_status launch_tc(p2s_ctx *ctx, int mode, const FieldGeom &g, int n, int C, const float *const *xw,
-                     float *const *y, const float *alpha, const float *beta_in, float *beta_out, int *status,
-                     cudaStream_t st);
+// One frame of a tensor-core launch: warped input, output, anchors of the
+// frame ([Ah][Aw][36]), its size; tiles_* and tile_base are filled by the launcher.
+struct TcFrame {
+    const float *xw;
+    float *y;
+    const float *alpha;
+    int H, W, Ah, Aw, tiles_x, tiles_y, tile_base;
+};
+constexpr int kMaxTcFrames = 256;  // frames per persistent launch (the table is a kernel parameter)
+p2s_status launch_tc(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
+                     float *beta_out, int *status, cudaStream_t st);
 constexpr int kTcFull = 0, kTcMlpOnly = 1, kTcBlurOnly = 2;
 
 // Network kernel: beta of n frames into the 16-bit operand layout
@@ -166,5 +183,6 @@ p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, v
 p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, float *const *y,
                              const void *beta16, int *status, cudaStream_t st);
 int scatter_segment_rows(const p2s_ctx *ctx, int H);
+p2s_status scatter_prepare(p2s_ctx *ctx);
 
 }  // namespace p2s

@@ -271,7 +271,7 @@ class Simulator:
                                    _stream_handle(stream)), "p2s_stage_mlp")
         return out
 
-    OPTIONS = {"scatter_segment_rows": 1}
+    OPTIONS = {"scatter_segment_rows": 1, "graphs": 2, "graph_instantiations": 3, "graph_updates": 4}
 
     def set_option(self, name: str, value: int):
         _check(lib().p2s_set_option(self.ctx, self.OPTIONS[name], int(value)), "p2s_set_option")

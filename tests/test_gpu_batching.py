@@ -1,0 +1,98 @@
+"""Batching machinery on the GPU: frames of uneven size in one persistent
+tensor-core launch, and p2s_simulate captured as a CUDA graph."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.fields import CorrParams
+from paper_2107_11627_gb300 import inputs
+
+from gpu_common import TOL_BF16, cfg2, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _sim(prec="fp16", form="gather", graphs=False):
+    from paper_2107_11627_gb300 import p2s
+
+    c = cfg2()
+    sim = p2s.Simulator(c["H"], c["taps"], c["layers"], anchor_spacing=8, corr_len_px=(16.0,), precision=prec,
+                        form=form)
+    if graphs:
+        sim.set_option("graphs", 1)
+    return sim
+
+
+def _frames(shapes, c=3, first=2000):
+    return [inputs.blob_image(h, w, c, first + i) for i, (h, w) in enumerate(shapes)]
+
+
+def test_uneven_batch_matches_oracle_and_is_batch_invariant():
+    """Mixed sizes and channel counts in one call; each frame equals the oracle and is
+    bit-identical to the same frame simulated alone (the gather kernel has no
+    order-dependent sums)."""
+    sim = _sim()
+    shapes = inputs.uneven_sizes(6, seed=5)
+    shapes = [(max(8, h // 4), max(8, w // 4)) for h, w in shapes]  # keep the oracle quick
+    xs = _frames(shapes) + [inputs.blob_image(40, 72, 1, 2100)]
+    dr = [0.5 + 0.9 * i for i in range(len(xs))]
+    seeds = [500 + i for i in range(len(xs))]
+    ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
+    sim.check()
+    for i in (0, len(xs) - 1, 3):
+        ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
+                                    CorrParams(8, (16.0,)), (33, 33), form="gather")
+        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_BF16, (i, shapes[i] if i < len(shapes) else None)
+    for i in (1, len(xs) - 1):
+        (alone,) = sim.simulate([torch.from_numpy(xs[i]).cuda()], [dr[i]], [seeds[i]])
+        assert torch.equal(alone, ys[i])
+
+
+@pytest.mark.parametrize("form", ["gather", "scatter"])
+def test_graph_mode_matches_plain_launches(form):
+    shapes = [(96, 160), (64, 64), (96, 160), (130, 70)]
+    xs = [torch.from_numpy(x).cuda() for x in _frames(shapes)]
+    plain = _sim(form=form)
+    graph = _sim(form=form, graphs=True)
+    for call in range(3):  # same signature: one instantiation, then in-place updates
+        dr = [1.0 + call, 2.0, 3.5, 5.0]
+        seeds = [100 * call + i for i in range(4)]
+        a = plain.simulate(xs, dr, seeds)
+        b = graph.simulate(xs, dr, seeds)
+        plain.check()
+        graph.check()
+        for u, v in zip(a, b):
+            if form == "gather":
+                assert torch.equal(u, v)
+            else:  # atomic adds at segment boundaries may differ in summation order
+                assert rel(v.cpu().numpy(), u.cpu().numpy()) < 1e-6
+    assert graph.get_option("graph_instantiations") == 1
+    assert graph.get_option("graph_updates") == 2
+    # a new signature instantiates a second graph
+    graph.simulate(xs[:2], [1.0, 2.0], [1, 2])
+    graph.check()
+    assert graph.get_option("graph_instantiations") == 2
+
+
+def test_graph_mode_on_the_default_stream_orders_with_the_caller():
+    """Graphs run on the context's own stream; results must be visible to work the
+    caller queues afterwards on its stream."""
+    sim = _sim(graphs=True)
+    x = torch.from_numpy(inputs.blob_image(64, 96, 3, 2200)).cuda()
+    outs = []
+    for k in range(3):
+        (y,) = sim.simulate([x], [2.0], [k])
+        outs.append(y.clone())  # queued on the caller's stream right after the call
+    sim.check()
+    ref = _sim()
+    for k in range(3):
+        (r,) = ref.simulate([x], [2.0], [k])
+        assert torch.equal(outs[k], r)
