@@ -208,15 +208,74 @@ p2s_status p2s_check(p2s_ctx *ctx, void *stream);
  *       one context must not overlap on the GPU in this mode.  Ignored while
  *       profiling.  0 (default): plain launches.
  *   P2S_OPT_GRAPH_INSTANTIATIONS, P2S_OPT_GRAPH_UPDATES  (read only) how many
- *       graphs were instantiated / updated in place so far. */
+ *       graphs were instantiated / updated in place so far.
+ *   P2S_OPT_GATHER_BAND_ROWS  tile height of the fused tensor-core gather
+ *       kernel: 16 or 32 output rows per 128-column tile (0 = default 32). */
 typedef enum {
     P2S_OPT_SCATTER_SEGMENT_ROWS = 1,
     P2S_OPT_GRAPHS = 2,
     P2S_OPT_GRAPH_INSTANTIATIONS = 3,
-    P2S_OPT_GRAPH_UPDATES = 4
+    P2S_OPT_GRAPH_UPDATES = 4,
+    P2S_OPT_GATHER_BAND_ROWS = 5
 } p2s_option;
 p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value);
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value);
+
+/* Autotuner (no counterpart in the paper).  Runs p2s_simulate on the given
+ * batch (device frames, written to `out`) once per candidate setting of the
+ * tile-shape option of the context's path (P2S_OPT_GATHER_BAND_ROWS for the
+ * tensor-core gather, P2S_OPT_SCATTER_SEGMENT_ROWS for the tensor-core
+ * scatter; the FP32 path has none), after one warm-up call times `reps`
+ * calls with CUDA events on `stream` (synchronising it), keeps the fastest
+ * setting in the context and reports every candidate in `res` (may be NULL).
+ * Arguments as p2s_simulate; reps >= 1. */
+typedef struct {
+    int option;       /* the p2s_option tuned (0 if the path has none) */
+    int n;            /* candidates tried */
+    int value[8];     /* candidate settings */
+    float ms[8];      /* mean milliseconds per call of each */
+    int best;         /* index of the setting kept */
+} p2s_tune_result;
+p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                        const unsigned long long *seeds, const p2s_image *out, void *stream, int reps,
+                        p2s_tune_result *res);
+
+/* ---- serving (no counterpart in the paper) -------------------------------- */
+
+/* A request loop over one context: single frames of any size, each with its
+ * own D/r0 and seed, submitted from host memory.  The context keeps the
+ * basis and weights resident; requests are admitted in arrival order while
+ * their device footprint (input, output, path scratch) fits in
+ * hbm_budget_bytes, and whatever is admitted when one of the
+ * max_inflight_batches stream slots frees is run as one p2s_simulate call
+ * (at most max_batch frames).  Batches of different slots overlap on the
+ * device; requests arriving meanwhile join the next batch (continuous
+ * batching).  Each request's result depends only on its own frame, D/r0 and
+ * seed.  Host buffers must stay valid until the request is done; pinned
+ * memory gives asynchronous copies.  The context must not be in graph mode
+ * and must not be used by other calls while the server exists. */
+typedef struct p2s_server p2s_server;
+typedef struct {
+    size_t hbm_budget_bytes;   /* > 0 */
+    int max_inflight_batches;  /* 1..16 */
+    int max_batch;             /* 1..256 */
+} p2s_server_config;
+typedef struct {
+    long long completed, batches, pending;
+    double mean_batch;         /* frames per batch so far */
+    size_t bytes_in_use, peak_bytes;
+} p2s_server_counters;
+p2s_status p2s_server_create(p2s_ctx *ctx, const p2s_server_config *cfg, p2s_server **out);
+/* Queues a request; *ticket identifies it.  ENOMEM if it alone exceeds the budget. */
+p2s_status p2s_server_submit(p2s_server *srv, const float *host_in, int H, int W, int C, float d_over_r0,
+                             unsigned long long seed, float *host_out, long long *ticket);
+/* Non-blocking: *done = 1 once out is written; latency_ms = completion - submission. */
+p2s_status p2s_server_poll(p2s_server *srv, long long ticket, int *done, double *latency_ms);
+/* Blocks up to timeout_s seconds; ETIMEOUT if still running. */
+p2s_status p2s_server_wait(p2s_server *srv, long long ticket, double timeout_s, double *latency_ms);
+p2s_status p2s_server_stats(p2s_server *srv, p2s_server_counters *out);
+/* Finishes queued and running requests, then releases the server. */
+void p2s_server_destroy(p2s_server *srv);
 
 /* ---- kernel timing ------------------------------------------------------- */
 

@@ -34,10 +34,8 @@ namespace p2s {
 namespace tc {
 
 constexpr int kStrip = 128;                    // output columns per tile (TMEM lanes)
-constexpr int kBand = 32;                      // output rows per tile
 constexpr int kHalo = 16;                      // 33 x 33 taps
 constexpr int kTaps = 2 * kHalo + 1;
-constexpr int kTR = kBand + 2 * kHalo;         // x tile rows
 constexpr int kTC = kStrip + 2 * kHalo;        // x tile columns
 constexpr int kKP = 112;                       // padded contraction depth
 constexpr int kKSteps = kKP / 16;
@@ -84,16 +82,23 @@ struct Params {
 
 // shared-memory layout
 constexpr int kOffRing = 0;
-constexpr int kOffXrg = kOffRing + kSlots * kSlot;             // float2 [kTR][kTC]
-constexpr int kOffXb = kOffXrg + kTR * kTC * 8;                // float  [kTR][kTC]
-constexpr int kOffBias = kOffXb + kTR * kTC * 4;               // 256 floats
-constexpr int kOffXchg = kOffBias + 256 * 4;                   // [128][6] floats
-constexpr int kOffBar = kOffXchg + kStrip * 6 * 4;             // mbarriers
 // ring full/empty, network stage handshakes, contraction buffer full/empty
 enum Bar { kFull0 = 0, kEmpty0 = 3, kA1b = 6, kD1b, kA2b, kD2b, kA3b, kD3b, kBetab, kDFull0 = 13, kDEmpty0 = 15, kNBar = 17 };
-constexpr int kOffMisc = kOffBar + kNBar * 8;                  // tmem base, abort flag
-constexpr int kSmemBytes = kOffMisc + 16 + 1024;               // + alignment slack
-static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+
+// Tile shape: 128 output columns x BAND output rows (BAND = 16 or 32); the x
+// tile with its halo is (BAND + 32) x 160 FP32 pixels in shared memory.
+template <int BAND>
+struct Lay {
+    static constexpr int TR = BAND + 2 * kHalo;                  // x tile rows
+    static constexpr int OffXrg = kOffRing + kSlots * kSlot;     // float2 [TR][kTC]
+    static constexpr int OffXb = OffXrg + TR * kTC * 8;          // float  [TR][kTC]
+    static constexpr int OffBias = OffXb + TR * kTC * 4;         // 256 floats
+    static constexpr int OffXchg = OffBias + 256 * 4;            // [128][6] floats
+    static constexpr int OffBar = OffXchg + kStrip * 6 * 4;      // mbarriers
+    static constexpr int OffMisc = OffBar + kNBar * 8;           // tmem base, abort flag
+    static constexpr int SmemBytes = OffMisc + 16 + 1024;        // + alignment slack
+    static_assert(SmemBytes <= 227 * 1024, "shared memory budget");
+};
 
 using tcc::Ctl;
 using tcc::drain_bar;
@@ -115,18 +120,19 @@ __device__ __forceinline__ int frame_of(const Params &p, int tile) {
     return lo;
 }
 
-template <int C>
+template <int C, int BAND>
 __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constant__ Params p) {
+    using L = Lay<BAND>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = ptx::smem_u32(sm);
-    float2 *xrg = (float2 *)(sm + kOffXrg);
-    float *xb = (float *)(sm + kOffXb);
-    float *sbias = (float *)(sm + kOffBias);
-    float *xchg = (float *)(sm + kOffXchg);
-    const uint32_t bar0 = sbase + kOffBar;
-    uint32_t *tmem_holder = (uint32_t *)(sm + kOffMisc);
-    volatile int *abort_flag = (volatile int *)(sm + kOffMisc + 4);
+    float2 *xrg = (float2 *)(sm + L::OffXrg);
+    float *xb = (float *)(sm + L::OffXb);
+    float *sbias = (float *)(sm + L::OffBias);
+    float *xchg = (float *)(sm + L::OffXchg);
+    const uint32_t bar0 = sbase + L::OffBar;
+    uint32_t *tmem_holder = (uint32_t *)(sm + L::OffMisc);
+    volatile int *abort_flag = (volatile int *)(sm + L::OffMisc + 4);
     auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Ctl ctl{abort_flag, p.status};
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
     auto n_pairs_of = [&](int tile) {
         const TcFrame &F = p.fr[frame_of(p, tile)];
         const int ty = (tile - F.tile_base) / F.tiles_x;
-        const int rows = min(kBand, F.H - ty * kBand);
+        const int rows = min(BAND, F.H - ty * BAND);
         return (rows + 1) >> 1;
     };
 
@@ -282,12 +288,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
             const TcFrame &F = p.fr[frame];
             const int lt = tile - F.tile_base;
             const int ty = lt / F.tiles_x, tx = lt - ty * F.tiles_x;
-            const int r_band = ty * kBand, c0 = tx * kStrip;
+            const int r_band = ty * BAND, c0 = tx * kStrip;
             const int npair = n_pairs_of(tile);
             if (do_blur) {
                 ptx::named_bar(1, kEpi);  // previous tile fully consumed
                 const float *x = F.xw;
-                for (int i = tid_e; i < kTR * kTC; i += kEpi) {
+                for (int i = tid_e; i < L::TR * kTC; i += kEpi) {
                     const int tr = i / kTC, tcol = i - tr * kTC;
                     const int gr = r_band - kHalo + tr, gc = c0 - kHalo + tcol;
                     float r = 0.f, g = 0.f, b = 0.f;
@@ -678,7 +684,7 @@ p2s_status tc_prepare(p2s_ctx *ctx) {
     return P2S_OK;
 }
 
-int tc_smem_bytes() { return kSmemBytes; }
+int tc_smem_bytes() { return Lay<32>::SmemBytes; }
 
 static p2s_status launch_tc_chunk(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
                                   float *beta_out, int *status, cudaStream_t st);
@@ -704,12 +710,13 @@ static p2s_status launch_tc_chunk(p2s_ctx *ctx, int mode, const TcFrame *frames,
                                   float *beta_out, int *status, cudaStream_t st) {
     thread_local Params p;  // large (frame table); copied into the launch by value
     std::memset(&p, 0, sizeof p);
+    const int band = ctx->tc.band_rows == 16 ? 16 : 32;
     int tiles = 0;
     double npx = 0.0;
     for (int i = 0; i < n; ++i) {
         TcFrame f = frames[i];
         f.tiles_x = (f.W + kStrip - 1) / kStrip;
-        f.tiles_y = (f.H + kBand - 1) / kBand;
+        f.tiles_y = (f.H + band - 1) / band;
         f.tile_base = tiles;
         tiles += f.tiles_x * f.tiles_y;
         npx += (double)f.H * f.W;
@@ -746,13 +753,17 @@ static p2s_status launch_tc_chunk(p2s_ctx *ctx, int mode, const TcFrame *frames,
                                             : 2.0 * (ctx->K * ctx->T + macs_net) * npx;
     ProfScope pr(ctx, st, mode == kFull ? "fused_tc_gather" : mode == kMlpOnly ? "mlp_tc" : "blur_tc_gather", flops,
                  npx * C * 8.0);
-    if (C == 3) {
-        P2S_CUDA(cudaFuncSetAttribute(fused_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-        fused_kernel<3><<<grid, kThreads, kSmemBytes, st>>>(p);
-    } else {
-        P2S_CUDA(cudaFuncSetAttribute(fused_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-        fused_kernel<1><<<grid, kThreads, kSmemBytes, st>>>(p);
-    }
+    auto go = [&](auto kern, int smem) -> p2s_status {
+        P2S_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        kern<<<grid, kThreads, smem, st>>>(p);
+        return P2S_OK;
+    };
+    p2s_status ls;
+    if (band == 16)
+        ls = C == 3 ? go(fused_kernel<3, 16>, Lay<16>::SmemBytes) : go(fused_kernel<1, 16>, Lay<16>::SmemBytes);
+    else
+        ls = C == 3 ? go(fused_kernel<3, 32>, Lay<32>::SmemBytes) : go(fused_kernel<1, 32>, Lay<32>::SmemBytes);
+    if (ls != P2S_OK) return ls;
     P2S_CUDA(cudaGetLastError());
     return P2S_OK;
 }

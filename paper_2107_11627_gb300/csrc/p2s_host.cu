@@ -527,6 +527,11 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
         ctx->use_graphs = value;
         return P2S_OK;
     }
+    if (option == P2S_OPT_GATHER_BAND_ROWS) {
+        if (value != 0 && value != 16 && value != 32) return einval("band rows must be 0, 16 or 32");
+        ctx->tc.band_rows = value;
+        return P2S_OK;
+    }
     return einval("unknown option");
 }
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
@@ -545,6 +550,10 @@ p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
     }
     if (option == P2S_OPT_GRAPH_UPDATES) {
         *value = (int)ctx->graph_updates;
+        return P2S_OK;
+    }
+    if (option == P2S_OPT_GATHER_BAND_ROWS) {
+        *value = ctx->tc.band_rows;
         return P2S_OK;
     }
     return einval("unknown option");
@@ -909,6 +918,64 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     Scratch sc{ctx, s, false};
     st = simulate_impl(ctx, frames, n, d_over_r0, seeds, out, s, sc);
     sc.release();
+    return st;
+}
+
+p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                        const unsigned long long *seeds, const p2s_image *out, void *stream, int reps,
+                        p2s_tune_result *res) {
+    p2s_status st = validate_simulate(ctx, frames, n, d_over_r0, seeds, out);
+    if (st != P2S_OK) return st;
+    if (reps < 1) return einval("reps must be >= 1");
+    const bool tc = ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16;
+    int option = 0;
+    std::vector<int> cand;
+    if (tc && ctx->form == P2S_GATHER) {
+        option = P2S_OPT_GATHER_BAND_ROWS;
+        cand = {32, 16};
+    } else if (tc && ctx->form == P2S_SCATTER) {
+        option = P2S_OPT_SCATTER_SEGMENT_ROWS;
+        cand = {32, 64, 128, 256, 1024};
+    }
+    p2s_tune_result r;
+    std::memset(&r, 0, sizeof r);
+    r.option = option;
+    if (cand.empty()) {
+        if (res) *res = r;
+        return P2S_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    P2S_CUDA(cudaEventCreate(&e0));
+    P2S_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (size_t c = 0; c < cand.size() && c < 8; ++c) {
+        if ((st = p2s_set_option(ctx, option, cand[c])) != P2S_OK) break;
+        if ((st = p2s_simulate(ctx, frames, n, d_over_r0, seeds, out, stream)) != P2S_OK) break;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < reps && st == P2S_OK; ++k) st = p2s_simulate(ctx, frames, n, d_over_r0, seeds, out, stream);
+        cudaEventRecord(e1, s);
+        if (st != P2S_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = P2S_ECUDA;
+            set_error("autotune: stream failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        r.value[r.n] = cand[c];
+        r.ms[r.n] = ms / reps;
+        if (r.ms[r.n] < best) {
+            best = r.ms[r.n];
+            r.best = r.n;
+        }
+        ++r.n;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != P2S_OK) return st;
+    st = p2s_set_option(ctx, option, r.value[r.best]);
+    if (res) *res = r;
     return st;
 }
 

@@ -60,6 +60,7 @@ struct TcPack {
     int ready = 0;
     void *d_Hs = nullptr;  // basis for the scatter kernel, tap-column-major [14][1104][8] 16-bit
     int seg_rows = 0;      // source rows per scatter work unit (0: default)
+    int band_rows = 0;     // output rows per fused gather tile: 16 or 32 (0: default 32)
 };
 
 // One B image of the tensor-core weight stream: byte offset and size in the

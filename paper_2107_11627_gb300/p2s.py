@@ -43,6 +43,19 @@ class p2s_kernel_stat(C.Structure):
                 ("bytes", C.c_double)]
 
 
+class p2s_tune_result(C.Structure):
+    _fields_ = [("option", C.c_int), ("n", C.c_int), ("value", C.c_int * 8), ("ms", C.c_float * 8), ("best", C.c_int)]
+
+
+class p2s_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight_batches", C.c_int), ("max_batch", C.c_int)]
+
+
+class p2s_server_counters(C.Structure):
+    _fields_ = [("completed", C.c_longlong), ("batches", C.c_longlong), ("pending", C.c_longlong),
+                ("mean_batch", C.c_double), ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t)]
+
+
 class p2s_geometry(C.Structure):
     _fields_ = [("anchors_h", C.c_int), ("anchors_w", C.c_int), ("torus_h", C.c_int), ("torus_w", C.c_int),
                 ("alpha_stride", C.c_int)]
@@ -66,6 +79,16 @@ _SIGS = {
     "p2s_stage_warp": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
     "p2s_stage_mlp": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "p2s_server_create": (C.c_int, [C.c_void_p, C.POINTER(p2s_server_config), C.POINTER(C.c_void_p)]),
+    "p2s_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong,
+                                    C.c_void_p, C.POINTER(C.c_longlong)]),
+    "p2s_server_poll": (C.c_int, [C.c_void_p, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "p2s_server_wait": (C.c_int, [C.c_void_p, C.c_longlong, C.c_double, C.POINTER(C.c_double)]),
+    "p2s_server_stats": (C.c_int, [C.c_void_p, C.POINTER(p2s_server_counters)]),
+    "p2s_server_destroy": (None, [C.c_void_p]),
+    "p2s_autotune": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_int, C.POINTER(C.c_float),
+                               C.POINTER(C.c_ulonglong), C.POINTER(p2s_image), C.c_void_p, C.c_int,
+                               C.POINTER(p2s_tune_result)]),
     "p2s_get_option": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "p2s_stage_mlp16": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_stage_blur": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
@@ -225,6 +248,25 @@ class Simulator:
                "p2s_simulate")
         return out
 
+    def autotune(self, frames, d_over_r0, seeds, out=None, reps: int = 2, stream=None):
+        """Times the path's tile-shape candidates on this batch, keeps the fastest.
+        Returns {"option": name or None, "candidates": {value: ms}, "best": value}."""
+        torch = _torch()
+        frames = list(frames)
+        n = len(frames)
+        if out is None:
+            out = [torch.empty_like(f) for f in frames]
+        dr, sd = self._meta(d_over_r0, seeds, n)
+        fi = (p2s_image * max(n, 1))(*[_image(f) for f in frames])
+        oi = (p2s_image * max(n, 1))(*[_image(o) for o in out])
+        r = p2s_tune_result()
+        _check(lib().p2s_autotune(self.ctx, fi, n, dr.ctypes.data_as(C.POINTER(C.c_float)),
+                                  sd.ctypes.data_as(C.POINTER(C.c_ulonglong)), oi, _stream_handle(stream), int(reps),
+                                  C.byref(r)), "p2s_autotune")
+        names = {v: k for k, v in self.OPTIONS.items()}
+        cands = {r.value[i]: float(r.ms[i]) for i in range(r.n)}
+        return {"option": names.get(r.option), "candidates": cands, "best": r.value[r.best] if r.n else None}
+
     def simulate_host(self, frames, d_over_r0, seeds, out=None, stream=None):
         """Host (NumPy float32) frames in and out; copies happen inside the call."""
         frames = list(frames)
@@ -271,7 +313,8 @@ class Simulator:
                                    _stream_handle(stream)), "p2s_stage_mlp")
         return out
 
-    OPTIONS = {"scatter_segment_rows": 1, "graphs": 2, "graph_instantiations": 3, "graph_updates": 4}
+    OPTIONS = {"scatter_segment_rows": 1, "graphs": 2, "graph_instantiations": 3, "graph_updates": 4,
+               "gather_band_rows": 5}
 
     def set_option(self, name: str, value: int):
         _check(lib().p2s_set_option(self.ctx, self.OPTIONS[name], int(value)), "p2s_set_option")
@@ -297,3 +340,59 @@ class Simulator:
         _check(lib().p2s_stage_blur(self.ctx, C.byref(_image(xw)), C.c_void_p(beta.data_ptr()), C.byref(_image(out)),
                                     _stream_handle(stream)), "p2s_stage_blur")
         return out
+
+
+class Server:
+    """Request loop over a Simulator (argument marshalling for the p2s_server_* calls).
+
+    submit() takes a host float32 [H, W, C] array and an output array of the same
+    shape; both must stay alive until the request is done (this object keeps
+    references until wait()/poll() reports it).  Pinned buffers copy asynchronously."""
+
+    def __init__(self, sim: "Simulator", hbm_budget_bytes: int, max_inflight: int = 4, max_batch: int = 16):
+        self.sim = sim
+        cfg = p2s_server_config(int(hbm_budget_bytes), int(max_inflight), int(max_batch))
+        h = C.c_void_p()
+        _check(lib().p2s_server_create(sim.ctx, C.byref(cfg), C.byref(h)), "p2s_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, x: np.ndarray, d_over_r0: float, seed: int, out: np.ndarray) -> int:
+        assert x.dtype == np.float32 and x.flags.c_contiguous and x.ndim == 3
+        assert out.shape == x.shape and out.dtype == np.float32 and out.flags.c_contiguous
+        t = C.c_longlong()
+        _check(lib().p2s_server_submit(self.h, C.c_void_p(x.ctypes.data), x.shape[0], x.shape[1], x.shape[2],
+                                       float(d_over_r0), int(seed), C.c_void_p(out.ctypes.data), C.byref(t)),
+               "p2s_server_submit")
+        self._keep[t.value] = (x, out)
+        return t.value
+
+    def poll(self, ticket: int):
+        done, lat = C.c_int(0), C.c_double(0.0)
+        _check(lib().p2s_server_poll(self.h, int(ticket), C.byref(done), C.byref(lat)), "p2s_server_poll")
+        if done.value:
+            self._keep.pop(ticket, None)
+        return bool(done.value), lat.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> float:
+        lat = C.c_double(0.0)
+        _check(lib().p2s_server_wait(self.h, int(ticket), float(timeout_s), C.byref(lat)), "p2s_server_wait")
+        self._keep.pop(ticket, None)
+        return lat.value
+
+    def stats(self) -> dict:
+        c = p2s_server_counters()
+        _check(lib().p2s_server_stats(self.h, C.byref(c)), "p2s_server_stats")
+        return {f: getattr(c, f) for f, _ in p2s_server_counters._fields_}
+
+    def close(self):
+        if self.h:
+            lib().p2s_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -96,3 +96,34 @@ def test_graph_mode_on_the_default_stream_orders_with_the_caller():
     for k in range(3):
         (r,) = ref.simulate([x], [2.0], [k])
         assert torch.equal(outs[k], r)
+
+
+def test_gather_band_16_equals_band_32():
+    """The tile height changes only how pixels are grouped, not their arithmetic."""
+    shapes = [(100, 150), (33, 260)]
+    xs = [torch.from_numpy(x).cuda() for x in _frames(shapes)]
+    a = _sim()
+    b = _sim()
+    b.set_option("gather_band_rows", 16)
+    ya = a.simulate(xs, [2.0, 3.0], [1, 2])
+    yb = b.simulate(xs, [2.0, 3.0], [1, 2])
+    a.check()
+    b.check()
+    for u, v in zip(ya, yb):
+        assert torch.equal(u, v)
+
+
+@pytest.mark.parametrize("form", ["gather", "scatter"])
+def test_autotune_picks_a_candidate_and_keeps_results(form):
+    sim = _sim(form=form)
+    shapes = [(96, 160), (64, 200)]
+    xs = [torch.from_numpy(x).cuda() for x in _frames(shapes)]
+    before = sim.simulate(xs, [2.0, 4.0], [3, 4])
+    r = sim.autotune(xs, [2.0, 4.0], [3, 4], reps=1)
+    assert r["option"] == ("gather_band_rows" if form == "gather" else "scatter_segment_rows")
+    assert len(r["candidates"]) >= 2 and r["best"] in r["candidates"]
+    assert sim.get_option(r["option"]) == r["best"]
+    after = sim.simulate(xs, [2.0, 4.0], [3, 4])
+    sim.check()
+    for u, v in zip(before, after):
+        assert rel(v.cpu().numpy(), u.cpu().numpy()) < 1e-6

@@ -1,0 +1,95 @@
+"""The serving loop on the GPU: continuous batching of mixed-size requests
+under an HBM budget; every result equals the frame simulated alone."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.fields import CorrParams
+from paper_2107_11627_gb300 import inputs
+
+from gpu_common import TOL_BF16, cfg2, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _sim(prec="fp16", form="gather"):
+    from paper_2107_11627_gb300 import p2s
+
+    c = cfg2()
+    return p2s.Simulator(c["H"], c["taps"], c["layers"], anchor_spacing=8, corr_len_px=(16.0,), precision=prec,
+                         form=form)
+
+
+def _requests(n, seed=11):
+    sizes = [(64, 64), (96, 160), (48, 200), (128, 72), (33, 33)]
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        h, w = sizes[i % len(sizes)]
+        x = inputs.blob_image(h, w, 3, 3000 + i)
+        reqs.append((x, float(rng.uniform(0.5, 6.0)), 7000 + i))
+    return reqs
+
+
+@pytest.mark.parametrize("form", ["gather", "scatter"])
+def test_results_equal_alone_and_in_the_mix(form):
+    from paper_2107_11627_gb300 import p2s
+
+    sim = _sim(form=form)
+    reqs = _requests(12)
+    srv = p2s.Server(sim, hbm_budget_bytes=1 << 30, max_inflight=3, max_batch=4)
+    outs = [np.zeros_like(x) for x, _, _ in reqs]
+    tickets = [srv.submit(x, dr, sd, o) for (x, dr, sd), o in zip(reqs, outs)]
+    lats = [srv.wait(t, 60.0) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["batches"] >= 3 and all(l > 0 for l in lats)
+    ref = _sim(form=form)
+    for (x, dr, sd), o in zip(reqs, outs):
+        (alone,) = ref.simulate([torch.from_numpy(x).cuda()], [dr], [sd])
+        a = alone.cpu().numpy()
+        if form == "gather":
+            assert np.array_equal(a, o)
+        else:
+            assert rel(o, a) < 1e-6
+    x, dr, sd = reqs[1]
+    want = oracle.frame.simulate(x.astype(np.float64), sd, dr, cfg2()["H"], cfg2()["layers"], CorrParams(8, (16.0,)),
+                                 (33, 33), form=form)
+    assert rel(outs[1], want.y) < TOL_BF16
+
+
+def test_admission_holds_the_budget():
+    """A budget that fits about one request: everything still completes, one frame per batch."""
+    from paper_2107_11627_gb300 import p2s
+
+    sim = _sim()
+    reqs = [(inputs.blob_image(96, 160, 3, 3100 + i), 1.0 + i, 8000 + i) for i in range(5)]
+    srv = p2s.Server(sim, hbm_budget_bytes=1_000_000, max_inflight=4, max_batch=8)
+    outs = [np.zeros_like(x) for x, _, _ in reqs]
+    tickets = [srv.submit(x, dr, sd, o) for (x, dr, sd), o in zip(reqs, outs)]
+    for t in tickets:
+        srv.wait(t, 60.0)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs)
+    assert st["peak_bytes"] <= 1_000_000
+    assert st["mean_batch"] == 1.0  # one 96 x 160 request holds ~0.73 MB of the 1 MB
+
+
+def test_request_larger_than_the_budget_is_refused():
+    from paper_2107_11627_gb300 import p2s
+
+    sim = _sim()
+    srv = p2s.Server(sim, hbm_budget_bytes=1 << 20, max_inflight=1, max_batch=1)
+    x = inputs.blob_image(512, 512, 3, 1)
+    with pytest.raises(p2s.P2SError):
+        srv.submit(x, 2.0, 1, np.zeros_like(x))
+    srv.close()
