@@ -161,6 +161,116 @@ def run_reference(args):
     return 0
 
 
+SERVE_SIZES = [(256, 256), (512, 512), (576, 1024), (720, 1280), (1080, 1920), (1152, 2048)]
+
+
+def run_batching(args, Hb, layers, frames=96, steps=5):
+    """96 RGB frames of uneven size (long side in {128..1024}, aspect 1..16:9), D/r0 ~ U[0.5, 6]:
+    autotuned tile shape, one persistent tensor-core launch per call, captured as a CUDA graph."""
+    import torch
+
+    from paper_2107_11627_gb300 import inputs, p2s
+
+    sizes = inputs.uneven_sizes(frames, seed=96)
+    xs = [torch.from_numpy(inputs.blob_image(h, w, CH, 5000 + i)).cuda() for i, (h, w) in enumerate(sizes)]
+    ys = [torch.empty_like(x) for x in xs]
+    dr = inputs.frame_strengths(frames, 0.5, 6.0, 9)
+    seeds = inputs.frame_seeds(frames, 2 * 10**6)
+    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,), precision=args.precision,
+                        form=args.form)
+    tune = sim.autotune(xs, dr, seeds, out=ys, reps=1)
+    sim.set_option("graphs", 1)
+    for _ in range(2):
+        sim.simulate(xs, dr, seeds, out=ys)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+    ev[0].record(stream)
+    for _ in range(steps):
+        sim.simulate(xs, dr, seeds, out=ys)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    sim.check()
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    mpx = sum(h * w for h, w in sizes) / 1e6
+    out = {"workload": f"{frames} RGB frames of uneven size (long side 128..1024, aspect 1..16:9), "
+                       f"{args.precision} {args.form}, autotuned, CUDA graph",
+           "frames_per_s": frames / (ms / 1e3), "mpix_per_s": mpx / (ms / 1e3), "ms_per_call": ms,
+           "mpix_per_call": mpx, "autotune": tune, "graph_instantiations": sim.get_option("graph_instantiations"),
+           "graph_updates": sim.get_option("graph_updates")}
+    sim.close()
+    return out
+
+
+def run_serving(args, Hb, layers, rate=200.0, seconds=4.0, saturate=256):
+    """Poisson arrivals of single RGB frames (sizes 256^2 .. 2048x1152, D/r0 ~ U[0.5, 6], own seed each)
+    into the request loop; p50/p99 latency from submission to result in host memory."""
+    import torch
+
+    from paper_2107_11627_gb300 import inputs, p2s
+
+    rng = np.random.default_rng(200)
+    pin_in = {hw: torch.from_numpy(inputs.blob_image(hw[0], hw[1], CH, 6000 + i)).pin_memory().numpy()
+              for i, hw in enumerate(SERVE_SIZES)}
+    ring = 6
+    pin_out = {hw: [torch.empty(hw + (CH,), dtype=torch.float32).pin_memory().numpy() for _ in range(ring)]
+               for hw in SERVE_SIZES}
+    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,), precision=args.precision,
+                        form=args.form)
+    srv = p2s.Server(sim, hbm_budget_bytes=8 << 30, max_inflight=4, max_batch=16)
+
+    def drive(arrivals):
+        t0 = time.perf_counter()
+        tickets = []
+        for k, t_arr in enumerate(arrivals):
+            hw = SERVE_SIZES[rng.integers(len(SERVE_SIZES))]
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            tickets.append(srv.submit(pin_in[hw], float(rng.uniform(0.5, 6.0)), 10**7 + k, pin_out[hw][k % ring]))
+        lat = [srv.wait(t, 120.0) for t in tickets]
+        return lat, time.perf_counter() - t0
+
+    drive(np.zeros(8))  # warm-up: kernels, pools
+    n = int(rate * seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    lat, el = drive(arrivals)
+    lat_sat, el_sat = drive(np.zeros(saturate))
+    st = srv.stats()
+    srv.close()
+    sim.close()
+    mean_px = float(np.mean([h * w for h, w in SERVE_SIZES]))
+    return {"workload": f"Poisson {rate:.0f} req/s for {seconds:.0f} s, RGB frames of "
+                        f"{'/'.join(f'{w}x{h}' for h, w in SERVE_SIZES)}, {args.precision} {args.form}",
+            "requests": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "frames_per_s": n / el, "saturation": {"requests": saturate, "frames_per_s": saturate / el_sat,
+                                                  "mpix_per_s": saturate * mean_px / 1e6 / el_sat,
+                                                  "p50_ms": float(np.percentile(lat_sat, 50))},
+            "mean_batch": st["mean_batch"], "peak_hbm_bytes": st["peak_bytes"],
+            "latency_includes": "host->device copy, path, device->host copy"}
+
+
+def fp32_batched_fps(Hb, layers, frames=8):
+    """The plain FP32 batched path at 512^2 RGB (scatter form), for comparison with serving."""
+    import torch
+
+    from paper_2107_11627_gb300 import inputs, p2s
+
+    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,), precision="fp32",
+                        form="scatter")
+    xs = [torch.from_numpy(x).cuda() for x in inputs.blob_batch(frames, HW, HW, CH, 1000)]
+    dr = inputs.frame_strengths(frames, 1.0, 5.0, 7)
+    seeds = inputs.frame_seeds(frames)
+    sim.simulate(xs, dr, seeds)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.simulate(xs, dr, seeds)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    sim.close()
+    return frames / el
+
+
 def main():
     global N_FRAMES
     ap = argparse.ArgumentParser()
@@ -174,6 +284,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=64, help="frames per step (profiling runs only)")
+    ap.add_argument("--no-batching", action="store_true", help="skip the uneven-size batching workload")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     args = ap.parse_args()
     N_FRAMES = args.frames
     if args.impl == "reference":
@@ -289,6 +401,14 @@ def main():
         acc = {"frame": 0, "vs": "FP64 oracle", "rel_l2": float(np.linalg.norm(err) / np.linalg.norm(y_ref)),
                "max_abs": float(np.abs(err).max())}
 
+    batching = serving = None
+    tc_path = args.precision in ("fp16", "bf16")
+    if rank == 0 and world == 1 and tc_path and not args.no_batching:
+        batching = run_batching(args, Hb, layers)
+    if rank == 0 and world == 1 and tc_path and not args.no_serving:
+        serving = run_serving(args, Hb, layers)
+        serving["fp32_batched_512_frames_per_s"] = fp32_batched_fps(Hb, layers)
+
     if rank == 0:
         dtype = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision]
         line = {"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -302,7 +422,7 @@ def main():
                 "latency_ms": {"step_p50": float(np.percentile(step_ms, 50)),
                                "step_p99": float(np.percentile(step_ms, 99)),
                                "frame_p50": float(np.percentile(step_ms, 50)) / N_FRAMES},
-                "roofline": roof, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "accuracy": acc, "batching": batching, "serving": serving, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in kstats]}
         print(json.dumps(line), flush=True)
     sim.close()
