@@ -33,6 +33,10 @@ N_FRAMES, HW, CH, K, TAPS, N_DICT = 64, 512, 3, 100, 33, 50_000
 DIMS = [33, 128, 128, 100]
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes per 512x512 RGB frame of each kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
+# full 64-frame launch under ncu, divided by 64); valid for the kernels as measured -- see profiles/
+DRAM_BYTES_PER_FRAME = {"fused_tc_gather": 399440128 / 64, "blur_tc_scatter": 4268525824 / 64,
+                        "net_tc": 3737016320 / 64}
 
 
 def workload_name(precision: str, form: str) -> str:
@@ -113,6 +117,27 @@ def dist():
         td.init_process_group("nccl")
         return td, rank, world, local
     return None, rank, world, local
+
+
+def replica_inputs(rank: int, n_frames: int):
+    """Rank r's share of a weak-scaling run: its own frames (image seeds, Philox seeds and
+    D/r0 draws disjoint from every other rank's); no data crosses ranks."""
+    from paper_2107_11627_gb300 import inputs
+
+    first = rank * n_frames
+    return {"image_seed": 1000 + first, "philox_seeds": inputs.frame_seeds(n_frames, 10**6 + first),
+            "d_over_r0": inputs.frame_strengths(n_frames, 1.0, 5.0, 7 + rank)}
+
+
+def max_over_ranks(td, value: float, device=None) -> float:
+    """The job's time is the slowest rank's (the only collective of the run)."""
+    if td is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
 
 
 def oracle_frame(H, layers, x, dr, seed, rows=None, form="scatter"):
@@ -301,9 +326,10 @@ def main():
     layers = inputs.mlp_weights(DIMS, 42)
     sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,),
                         precision=args.precision, form=args.form)
-    xs_host = inputs.blob_batch(N_FRAMES, HW, HW, CH, 1000 + rank * N_FRAMES)
-    dr = inputs.frame_strengths(N_FRAMES, 1.0, 5.0, 7 + rank)
-    seeds = inputs.frame_seeds(N_FRAMES, 10**6 + rank * N_FRAMES)
+    share = replica_inputs(rank, N_FRAMES)
+    xs_host = inputs.blob_batch(N_FRAMES, HW, HW, CH, share["image_seed"])
+    dr = share["d_over_r0"]
+    seeds = share["philox_seeds"]
     xs = [torch.from_numpy(x).cuda() for x in xs_host]
     ys = [torch.empty_like(x) for x in xs]
     stream = torch.cuda.current_stream()
@@ -336,10 +362,7 @@ def main():
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     kstats = sim.profile_read()
-    if td is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(td, total_ms, "cuda")
     frames_total = N_FRAMES * args.steps * world
     fps = frames_total / (total_ms / 1e3)
     mpix = fps * HW * HW / 1e6
@@ -359,8 +382,11 @@ def main():
         elif dom["flops"] > 0:
             peak = peaks["bf16_tflops_sustained"]
             achieved = dom["flops"] / dom["launches"] / avg_s / 1e12
+            tb = DRAM_BYTES_PER_FRAME.get(dom["name"])
+            traffic = tb * N_FRAMES if (tb is not None and HW == 512) else None
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": dom["name"],
+                    "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu)",
+                    "kernel": dom["name"],
                     "peak_source": f"{peak_src} bf16_tflops_sustained"}
         else:
             peak = peaks["hbm_gbs"]
@@ -382,10 +408,7 @@ def main():
         for _ in range(args.e2e_steps):
             sim.simulate_host(hin, dr, seeds, out=hout)
         el = time.perf_counter() - t0
-        if td is not None:
-            t = torch.tensor([el], device="cuda")
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(td, el, "cuda")
         bytes_step = N_FRAMES * HW * HW * CH * 4
         e2e = {"value": N_FRAMES * args.e2e_steps * world / el, "unit": "frames/s",
                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step}
