@@ -59,7 +59,9 @@ typedef enum {
 /* Which PSF a tap uses (Sec. 3.1):
  *   SCATTER  y_c[p + o(t)] += G[p, t] x_c[p]   source pixel's PSF, y = sum_k h_k * (beta_k . x)
  *   GATHER   y_c[q] += G[q, t] x_c[q - o(t)]   output pixel's PSF, Eq. 5
- *   FFT      the scatter form evaluated by batched FFTs (comparison variant)
+ *   FFT      the scatter form evaluated by batched FFTs (comparison variant;
+ *            FP32 precision only, frames up to 2016 pixels per side: the
+ *            transform sizes are powers of two >= H + 32, W + 32, at most 2048)
  * with G[p, t] = sum_k beta[p, k] H[k, t] and o(t) = (ty - taps_h/2, tx - taps_w/2). */
 typedef enum { P2S_SCATTER = 0, P2S_GATHER = 1, P2S_FFT = 2 } p2s_blur_form;
 

@@ -10,6 +10,7 @@
 // column pass that the anchors use are kept.
 #include <stdint.h>
 
+#include "fft_smem.cuh"
 #include "p2s_internal.h"
 
 namespace p2s {
@@ -80,35 +81,8 @@ __global__ void noise_kernel(unsigned long long seed, int mode, long long n, flo
         if (4 * q + i < n) out[4 * q + i] = z[i];
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// Radix-2 Stockham FFT of R rows of length N (power of two) held in `a`,
-// ping-ponging with `b`; natural order in and out.  All threads take part.
-// Returns the buffer that holds the result.  tw[m] = exp(-2 pi i m / N).
-__device__ float2 *fft_rows(float2 *a, float2 *b, const float2 *tw, int N, int R, bool inverse) {
-    const int half = N >> 1;
-    for (int ns = 1; ns < N; ns <<= 1) {
-        const int tstep = N / (2 * ns);
-        for (int idx = threadIdx.x; idx < R * half; idx += blockDim.x) {
-            const int r = idx / half, j = idx - r * half;
-            const int k = j & (ns - 1);
-            const float2 v0 = a[r * N + j];
-            float2 w = tw[k * tstep];
-            if (inverse) w.y = -w.y;
-            const float2 v1 = cmul(a[r * N + j + half], w);
-            const int d = ((j - k) << 1) + k;
-            b[r * N + d] = make_float2(v0.x + v1.x, v0.y + v1.y);
-            b[r * N + d + ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
-        }
-        __syncthreads();
-        float2 *t = a;
-        a = b;
-        b = t;
-    }
-    return a;
-}
+using fftsm::cmul;
+using fftsm::fft_rows;
 
 // Row pass: white noise rows (y0, y0+1) packed as one complex row, filtered
 // along x; columns [0, Aw) of both rows go to t[frame][mode][y][x].

@@ -227,7 +227,7 @@ p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr
     if (!(precision == P2S_FP32 || precision == P2S_BF16 || precision == P2S_FP16 || precision == P2S_FP8E4M3))
         return einval("unknown precision");
     const bool tc_prec = precision == P2S_BF16 || precision == P2S_FP16;
-    if (form == P2S_FFT || precision == P2S_FP8E4M3) {
+    if (precision == P2S_FP8E4M3 || (form == P2S_FFT && precision != P2S_FP32)) {
         set_error("precision/form pair not built yet");
         return P2S_EUNSUPPORTED;
     }
@@ -356,6 +356,8 @@ void p2s_destroy(p2s_ctx *ctx) {
     cudaFree(ctx->tc.d_H);
     cudaFree(ctx->tc.d_bias);
     cudaFree(ctx->tc.d_Hs);
+    for (auto &kv : ctx->fft_tw) cudaFree(kv.second);
+    for (auto &kv : ctx->fft_basis) cudaFree(kv.second);
     for (auto &kv : ctx->graphs)
         if (kv.second) cudaGraphExecDestroy(kv.second);
     cudaFree(ctx->arena);
@@ -593,6 +595,7 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
         const TcFrame f{xw->data, out->data, nullptr, xw->H, xw->W, g.Ah, g.Aw, 0, 0, 0};
         return launch_tc(ctx, kTcBlurOnly, &f, 1, xw->C, beta, nullptr, ctx->d_status, (cudaStream_t)stream);
     }
+    if (ctx->form == P2S_FFT) return launch_blur_fft(ctx, xw->H, xw->W, xw->C, 1, ip, beta, op, (cudaStream_t)stream);
     return launch_blur_simt(ctx, xw->H, xw->W, xw->C, 1, ip, beta, op, ctx->form, (cudaStream_t)stream);
 }
 
@@ -699,7 +702,9 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
             if (st == P2S_OK) st = launch_scatter_tc(ctx, H, W, C, nb, xwp, op, beta, ctx->d_status, s);
         } else {
             if (st == P2S_OK) st = launch_mlp_simt(ctx, g, nb, alpha, beta, s);
-            if (st == P2S_OK) st = launch_blur_simt(ctx, H, W, C, nb, xwp, beta, op, ctx->form, s);
+            if (st == P2S_OK)
+                st = ctx->form == P2S_FFT ? launch_blur_fft(ctx, H, W, C, nb, xwp, beta, op, s)
+                                          : launch_blur_simt(ctx, H, W, C, nb, xwp, beta, op, ctx->form, s);
         }
         sc.rewind(m0);
         if (st != P2S_OK) return st;
@@ -914,7 +919,8 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     p2s_status st = validate_simulate(ctx, frames, n, d_over_r0, seeds, out);
     if (st != P2S_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (ctx->use_graphs && !ctx->profiling && n > 0) return simulate_graph(ctx, frames, n, d_over_r0, seeds, out, s);
+    if (ctx->use_graphs && !ctx->profiling && n > 0 && ctx->form != P2S_FFT)
+        return simulate_graph(ctx, frames, n, d_over_r0, seeds, out, s);
     Scratch sc{ctx, s, false};
     st = simulate_impl(ctx, frames, n, d_over_r0, seeds, out, s, sc);
     sc.release();

@@ -108,6 +108,9 @@ struct p2s_ctx {
     // staging for p2s_simulate_host
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    // FFT blur variant: twiddles by length, basis spectra by (Fh << 16 | Fw)
+    std::map<int, void *> fft_tw;
+    std::map<long long, void *> fft_basis;
     // CUDA graphs of p2s_simulate (P2S_OPT_GRAPHS): scratch arena, internal
     // capture stream, instantiated graphs by batch signature
     int use_graphs = 0;
@@ -184,6 +187,9 @@ p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, v
 p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, float *const *y,
                              const void *beta16, int *status, cudaStream_t st);
 int scatter_segment_rows(const p2s_ctx *ctx, int H);
+// FFT evaluation of the scatter blur (FP32) from FP32 beta [n][H][W][K].
+p2s_status launch_blur_fft(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, const float *beta,
+                           float *const *y, cudaStream_t st);
 p2s_status scatter_prepare(p2s_ctx *ctx);
 
 }  // namespace p2s
