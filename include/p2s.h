@@ -195,6 +195,13 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
  * P2S_ECUDA if the stream reports an error, P2S_OK otherwise. */
 p2s_status p2s_check(p2s_ctx *ctx, void *stream);
 
+/* Self-test of that mechanism (no counterpart in the paper): enqueues one
+ * block whose bounded mbarrier wait has nothing to wait for; after about
+ * 0.1 s it gives up and sets the status word exactly as a stalled pipeline
+ * stage would, so the next p2s_check returns P2S_ETIMEOUT (and clears it).
+ * Nothing faults or hangs; the context stays usable. */
+p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
+
 /* ---- tuning --------------------------------------------------------------- */
 
 /* Tunable launch parameters (no counterpart in the paper; results do not

@@ -30,7 +30,7 @@ using fftsm::fft_rows;
 
 constexpr int kThreads = 256;
 constexpr int kMaxF = 2048;
-constexpr int kRowElems = 8192;  // complex elements per row-pass ping-pong buffer
+constexpr int kRowElems = 4096;  // complex elements per row-pass ping-pong buffer (>= 2 rows of 2048)
 
 // ---- 1. beta [H][W][K] -> [K][H][W] -------------------------------------------
 __global__ void transpose_beta(const float *__restrict__ in, float *__restrict__ out, int npx, int K) {
@@ -311,11 +311,15 @@ p2s_status launch_blur_fft(p2s_ctx *ctx, int H, int W, int C, int n, const float
     P2S_CUDA(cudaFuncSetAttribute(row_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
     const double flops = 2.0 * ctx->K * ctx->T * (double)npx;  // the direct form's work, for comparison
     for (int i = 0; i < n; ++i) {
-        ProfScope pr(ctx, st, "blur_fft", flops, (double)npx * (C * 8.0 + K * 4.0));
-        transpose_beta<<<dim3((npx + 31) / 32, (K + 31) / 32), dim3(32, 8), 0, st>>>(beta + (size_t)i * npx * K, betaT,
-                                                                                    npx, K);
-        RowSrc src{0, betaT, xw[i], nullptr, H, W, C, K, 0, 0};
-        row_r2c<<<dim3((K * C + 1) / 2, (H + RB - 1) / RB), kThreads, smem_r, st>>>(src, K * C, H, Fh, Fw, RB, tww, Z);
+        {
+            ProfScope pr(ctx, st, "blur_fft_rows", flops, (double)npx * (C * 4.0 + K * 8.0) + (double)z_bytes);
+            transpose_beta<<<dim3((npx + 31) / 32, (K + 31) / 32), dim3(32, 8), 0, st>>>(beta + (size_t)i * npx * K,
+                                                                                        betaT, npx, K);
+            RowSrc src{0, betaT, xw[i], nullptr, H, W, C, K, 0, 0};
+            row_r2c<<<dim3((K * C + 1) / 2, (H + RB - 1) / RB), kThreads, smem_r, st>>>(src, K * C, H, Fh, Fw, RB, tww,
+                                                                                          Z);
+        }
+        ProfScope pr(ctx, st, "blur_fft_cols", 0.0, (double)z_bytes + (double)K * nu * Fh * 8.0 + (double)npx * C * 4.0);
         if (C == 3) {
             P2S_CUDA(cudaFuncSetAttribute(col_mac<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
             col_mac<3><<<nu, kThreads, smem_c, st>>>(Z, Hk, K, H, Fh, nu, twh, Y);

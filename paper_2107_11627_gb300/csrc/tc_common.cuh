@@ -29,14 +29,15 @@ struct Ctl {
 // Bounded wait (about 2 s at 2 GHz); on timeout flags the CTA and the status
 // word.  Once the CTA is flagged every wait returns false at once, so all
 // roles run their (data-independent) loops to the end and meet at teardown.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Ctl &ctl, int code) {
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Ctl &ctl, int code,
+                                         long long limit = 4000000000ll) {
     if (ptx::mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     for (int spins = 0;; ++spins) {
         if (ptx::mbar_try(bar, parity)) return true;
         if (*ctl.abort) return false;
         if (spins > 4) __nanosleep(spins < 64 ? 32 : 128);  // leave issue slots to working warps
-        if (clock64() - t0 > 4000000000ll) {
+        if (clock64() - t0 > limit) {
             *ctl.abort = 1;
             atomicOr(ctl.status, code);
             return false;

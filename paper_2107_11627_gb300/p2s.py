@@ -79,6 +79,7 @@ _SIGS = {
     "p2s_stage_warp": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
     "p2s_stage_mlp": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "p2s_selftest_stall": (C.c_int, [C.c_void_p, C.c_void_p]),
     "p2s_server_create": (C.c_int, [C.c_void_p, C.POINTER(p2s_server_config), C.POINTER(C.c_void_p)]),
     "p2s_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong,
                                     C.c_void_p, C.POINTER(C.c_longlong)]),
@@ -312,6 +313,9 @@ class Simulator:
         _check(lib().p2s_stage_mlp(self.ctx, H, W, C.c_void_p(alpha.data_ptr()), C.c_void_p(out.data_ptr()),
                                    _stream_handle(stream)), "p2s_stage_mlp")
         return out
+
+    def selftest_stall(self, stream=None):
+        _check(lib().p2s_selftest_stall(self.ctx, _stream_handle(stream)), "p2s_selftest_stall")
 
     OPTIONS = {"scatter_segment_rows": 1, "graphs": 2, "graph_instantiations": 3, "graph_updates": 4,
                "gather_band_rows": 5}
