@@ -473,7 +473,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                                 wg[m] = rg.y;
                                 wb[m] = (C == 3) ? xb[base + m * kTC] : 0.f;
                             }
-                            ptx::tmem_wait_ld();
+                            ptx::tmem_wait_ld_dep(g0);
+                            ptx::tmem_wait_ld_dep(g1);
                             float a[16], bb[16];
 #pragma unroll
                             for (int t = 0; t < 16; ++t) {
