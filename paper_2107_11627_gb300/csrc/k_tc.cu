@@ -12,8 +12,10 @@
 //             rows; the last tap row as a final N = 48 chunk);
 //   gather    y_c[q] += G[q, t] x_c[q - o(t)] on the CUDA cores: each thread
 //             owns one output column of the row pair, walks a tap column with
-//             a 33-row window of x in registers (x staged as FP32 in shared
-//             memory), accumulates in FP32.
+//             a 33-row window of x in registers (x staged in shared memory as
+//             FP16 RGB in 8 bytes, widened to FP32 on load: 2/3 of the FP32
+//             staging traffic, the contraction's largest shared-memory stream),
+//             accumulates in FP32.
 // Roles: warp 0 issues MMAs (one thread), warp 1 streams weights and basis
 // chunks into a 3-slot shared-memory ring with 1-D bulk copies, warps 2..9
 // (two per TMEM lane quadrant) convert between layers and run the gather;
@@ -90,9 +92,8 @@ enum Bar { kFull0 = 0, kEmpty0 = 3, kA1b = 6, kD1b, kA2b, kD2b, kA3b, kD3b, kBet
 template <int BAND>
 struct Lay {
     static constexpr int TR = BAND + 2 * kHalo;                  // x tile rows
-    static constexpr int OffXrg = kOffRing + kSlots * kSlot;     // float2 [TR][kTC]
-    static constexpr int OffXb = OffXrg + TR * kTC * 8;          // float  [TR][kTC]
-    static constexpr int OffBias = OffXb + TR * kTC * 4;         // 256 floats
+    static constexpr int OffX = kOffRing + kSlots * kSlot;       // uint2 [TR][kTC]: (R, G, B, 0) as FP16
+    static constexpr int OffBias = OffX + TR * kTC * 8;          // 256 floats
     static constexpr int OffXchg = OffBias + 256 * 4;            // [128][6] floats
     static constexpr int OffBar = OffXchg + kStrip * 6 * 4;      // mbarriers
     static constexpr int OffMisc = OffBar + kNBar * 8;           // tmem base, abort flag
@@ -126,8 +127,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = ptx::smem_u32(sm);
-    float2 *xrg = (float2 *)(sm + L::OffXrg);
-    float *xb = (float *)(sm + L::OffXb);
+    uint2 *x16 = (uint2 *)(sm + L::OffX);
     float *sbias = (float *)(sm + L::OffBias);
     float *xchg = (float *)(sm + L::OffXchg);
     const uint32_t bar0 = sbase + L::OffBar;
@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                             b = __ldg(px + 2);
                         }
                     }
-                    xrg[i] = make_float2(r, g);
-                    xb[i] = b;
+                    const __half2 rg = __floats2half2_rn(r, g), b0 = __floats2half2_rn(b, 0.f);
+                    x16[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&rg), *reinterpret_cast<const uint32_t *>(&b0));
                 }
                 ptx::named_bar(1, kEpi);
             }
@@ -468,10 +468,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                             const int base = (2 * rp + 1 + jlo) * kTC + col + 32 - txx;
 #pragma unroll
                             for (int m = 0; m < 17; ++m) {
-                                const float2 rg = xrg[base + m * kTC];
+                                const uint2 v = x16[base + m * kTC];
+                                const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
                                 wr[m] = rg.x;
                                 wg[m] = rg.y;
-                                wb[m] = (C == 3) ? xb[base + m * kTC] : 0.f;
+                                wb[m] = (C == 3) ? __low2float(*reinterpret_cast<const __half2 *>(&v.y)) : 0.f;
                             }
                             ptx::tmem_wait_ld_dep(g0);
                             ptx::tmem_wait_ld_dep(g1);
@@ -514,14 +515,16 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                                 const int txx = 17 * half + q;
                                 const int i0 = (2 * rp) * kTC + col + 32 - txx, i1 = i0 + kTC;
                                 const float a = __uint_as_float(g0[q]), b2 = __uint_as_float(g1[q]);
-                                const float2 rg0 = xrg[i0], rg1 = xrg[i1];
+                                const uint2 v0 = x16[i0], v1 = x16[i1];
+                                const float2 rg0 = __half22float2(*reinterpret_cast<const __half2 *>(&v0.x));
+                                const float2 rg1 = __half22float2(*reinterpret_cast<const __half2 *>(&v1.x));
                                 acc[0][0] = fmaf(a, rg0.x, acc[0][0]);
                                 acc[1][0] = fmaf(b2, rg1.x, acc[1][0]);
                                 if (C == 3) {
                                     acc[0][1] = fmaf(a, rg0.y, acc[0][1]);
-                                    acc[0][2] = fmaf(a, xb[i0], acc[0][2]);
+                                    acc[0][2] = fmaf(a, __low2float(*reinterpret_cast<const __half2 *>(&v0.y)), acc[0][2]);
                                     acc[1][1] = fmaf(b2, rg1.y, acc[1][1]);
-                                    acc[1][2] = fmaf(b2, xb[i1], acc[1][2]);
+                                    acc[1][2] = fmaf(b2, __low2float(*reinterpret_cast<const __half2 *>(&v1.y)), acc[1][2]);
                                 }
                             }
                         }

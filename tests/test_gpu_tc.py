@@ -64,15 +64,17 @@ def test_tc_blur_stage_fp16(c, h, w):
 
 
 def test_tc_blur_stage_bf16_rounding_points():
-    """BF16 operands: the kernel must round exactly beta and H to BF16 (checked
-    against the oracle with those two tensors rounded), everything else FP32."""
+    """BF16 operands: the kernel must round exactly beta and H to BF16 and the staged
+    x_w window to FP16 (checked against the oracle with those three tensors rounded),
+    everything else FP32."""
     sim = _sim("bf16")
     rng = np.random.default_rng(32)
     h, w = 48, 160
     xw = inputs.blob_image(h, w, 3, 1004)
     beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
     y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
-    emu = oracle.blur.gather(xw.astype(np.float64), bf16(beta), bf16(cfg2()["H"]), 33, 33)
+    x16 = xw.astype(np.float16).astype(np.float64)  # round-to-nearest-even, as the kernel stages it
+    emu = oracle.blur.gather(x16, bf16(beta), bf16(cfg2()["H"]), 33, 33)
     assert rel(y, emu) < 2e-5, rel(y, emu)
 
 
