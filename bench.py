@@ -35,7 +35,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per 512x512 RGB frame of each kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
 # full 64-frame launch under ncu, divided by 64); valid for the kernels as measured -- see profiles/
-DRAM_BYTES_PER_FRAME = {"fused_tc_gather": 399440128 / 64, "blur_tc_scatter": 4268525824 / 64,
+DRAM_BYTES_PER_FRAME = {"fused_tc_gather": 400204032 / 64, "blur_tc_scatter": 4268525824 / 64,
                         "net_tc": 3737016320 / 64}
 
 

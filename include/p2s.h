@@ -219,13 +219,18 @@ p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
  *   P2S_OPT_GRAPH_INSTANTIATIONS, P2S_OPT_GRAPH_UPDATES  (read only) how many
  *       graphs were instantiated / updated in place so far.
  *   P2S_OPT_GATHER_BAND_ROWS  tile height of the fused tensor-core gather
- *       kernel: 16 or 32 output rows per 128-column tile (0 = default 32). */
+ *       kernel: 16 or 32 output rows per 128-column tile (0 = default 32).
+ *   P2S_OPT_BLUR_THEN_WARP  1: p2s_simulate blurs the input first and applies
+ *       the tilt warp to the blurred frame, the order of the collapsed model
+ *       (Sec. 2.2: the turbulent PSF is a tilt-free PSF shifted by the tilt);
+ *       0 (default): warp, then blur. */
 typedef enum {
     P2S_OPT_SCATTER_SEGMENT_ROWS = 1,
     P2S_OPT_GRAPHS = 2,
     P2S_OPT_GRAPH_INSTANTIATIONS = 3,
     P2S_OPT_GRAPH_UPDATES = 4,
-    P2S_OPT_GATHER_BAND_ROWS = 5
+    P2S_OPT_GATHER_BAND_ROWS = 5,
+    P2S_OPT_BLUR_THEN_WARP = 6
 } p2s_option;
 p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value);
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value);

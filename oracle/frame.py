@@ -43,8 +43,12 @@ def mlp_emulated(v, layers, rnd):
 
 def simulate(x: np.ndarray, seed: int, d_over_r0: float, Hb: np.ndarray, layers, p: fields.CorrParams,
              taps: tuple[int, int], kap: float | None = None, form: str = "scatter", emulate: str | None = None,
-             L: np.ndarray | None = None) -> Stages:
-    """The full path on one frame x [H, W, C] (float), FP64 throughout unless `emulate`."""
+             L: np.ndarray | None = None, order: str = "warp_blur") -> Stages:
+    """The full path on one frame x [H, W, C] (float), FP64 throughout unless `emulate`.
+
+    order "warp_blur": y = blur(warp(x)), the simulator's default; "blur_warp": y = warp(blur(x)),
+    the collapsed model's order of Sec. 2.2 (the blurred image shifted by the tilts).  In the
+    second case Stages.xw holds the unwarped input."""
     h, w = x.shape[:2]
     if L is None:
         L = noll.cholesky_lower(noll.noll_cov(36))
@@ -52,7 +56,9 @@ def simulate(x: np.ndarray, seed: int, d_over_r0: float, Hb: np.ndarray, layers,
         kap = warp.kappa()
     aa = fields.alpha_anchors(seed, d_over_r0, h, w, p, L)
     ap = fields.alpha_pixels(aa, h, w, p.anchor_spacing)
-    xw = warp.warp(x, ap, kap)
+    if order not in ("warp_blur", "blur_warp"):
+        raise ValueError(order)
+    xw = warp.warp(x, ap, kap) if order == "warp_blur" else x
     hi = ap[..., 2:]
     if emulate == "bf16":
         beta = bf16(mlp_emulated(hi, layers, bf16))
@@ -64,6 +70,8 @@ def simulate(x: np.ndarray, seed: int, d_over_r0: float, Hb: np.ndarray, layers,
         raise ValueError(emulate)
     fn = blur.scatter if form == "scatter" else blur.gather
     y = fn(xw, beta, Hb_used, taps[0], taps[1])
+    if order == "blur_warp":
+        y = warp.warp(y, ap, kap)
     return Stages(aa, ap, xw, beta, y)
 
 

@@ -534,6 +534,11 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
         ctx->tc.band_rows = value;
         return P2S_OK;
     }
+    if (option == P2S_OPT_BLUR_THEN_WARP) {
+        if (value != 0 && value != 1) return einval("blur-then-warp option is 0 or 1");
+        ctx->blur_then_warp = value;
+        return P2S_OK;
+    }
     return einval("unknown option");
 }
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
@@ -556,6 +561,10 @@ p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
     }
     if (option == P2S_OPT_GATHER_BAND_ROWS) {
         *value = ctx->tc.band_rows;
+        return P2S_OK;
+    }
+    if (option == P2S_OPT_BLUR_THEN_WARP) {
+        *value = ctx->blur_then_warp;
         return P2S_OK;
     }
     return einval("unknown option");
@@ -696,15 +705,29 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
             xwp[i] = xwm[i];
         }
         st = launch_fields(ctx, g, fb, alpha, fscr, s);
-        if (st == P2S_OK) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
+        // warp then blur (default), or blur the input then warp the result (Sec. 2.2 order);
+        // in the second case the x_w buffer holds the blurred, not yet warped frames
+        const bool bw = ctx->blur_then_warp;
+        float *blur_out[kMaxBatch];
+        for (int i = 0; i < nb; ++i) {
+            blur_out[i] = bw ? xwm[i] : op[i];
+            if (bw) xwp[i] = ip[i];
+        }
+        if (st == P2S_OK && !bw) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
+        float *const *bop = blur_out;
         if (tc && ctx->form == P2S_SCATTER) {
             if (st == P2S_OK) st = launch_net16(ctx, g, nb, alpha, beta, 1, ctx->d_status, s);
-            if (st == P2S_OK) st = launch_scatter_tc(ctx, H, W, C, nb, xwp, op, beta, ctx->d_status, s);
+            if (st == P2S_OK) st = launch_scatter_tc(ctx, H, W, C, nb, xwp, bop, beta, ctx->d_status, s);
         } else {
             if (st == P2S_OK) st = launch_mlp_simt(ctx, g, nb, alpha, beta, s);
             if (st == P2S_OK)
-                st = ctx->form == P2S_FFT ? launch_blur_fft(ctx, H, W, C, nb, xwp, beta, op, s)
-                                          : launch_blur_simt(ctx, H, W, C, nb, xwp, beta, op, ctx->form, s);
+                st = ctx->form == P2S_FFT ? launch_blur_fft(ctx, H, W, C, nb, xwp, beta, bop, s)
+                                          : launch_blur_simt(ctx, H, W, C, nb, xwp, beta, bop, ctx->form, s);
+        }
+        if (st == P2S_OK && bw) {
+            const float *bin[kMaxBatch];
+            for (int i = 0; i < nb; ++i) bin[i] = xwm[i];
+            st = launch_warp(ctx, g, nb, bin, alpha, op, C, s);
         }
         sc.rewind(m0);
         if (st != P2S_OK) return st;
@@ -719,6 +742,14 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
                                      const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s,
                                      Scratch &sc) {
     std::vector<TcFrame> tf[2];  // C = 1, C = 3
+    struct PostWarp {
+        FieldGeom g;
+        int C;
+        const float *in;
+        const float *alpha;
+        float *out;
+    };
+    std::vector<PostWarp> post_warp;
     std::vector<char> done(n, 0);
     std::vector<int> idx;
     p2s_status st = P2S_OK;
@@ -760,11 +791,15 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             float *xw = (float *)(buf + a_bytes + f_bytes);
             for (int k = 0; k < nb; ++k) xwm[k] = xw + (size_t)k * npx * C;
             st = launch_fields(ctx, g, fb, alpha, buf + a_bytes, s);
-            if (st == P2S_OK) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
+            const bool bw = ctx->blur_then_warp;
+            if (st == P2S_OK && !bw) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
             for (int k = 0; k < nb; ++k) {
                 const int f = idx[i0 + k];
-                tf[C == 3 ? 1 : 0].push_back(TcFrame{xwm[k], out[f].data, alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride,
-                                                     H, W, g.Ah, g.Aw, 0, 0, 0});
+                const float *a_k = alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride;
+                // blur-then-warp: the fused launch blurs the input into x_w, a warp follows
+                tf[C == 3 ? 1 : 0].push_back(
+                    TcFrame{bw ? ip[k] : xwm[k], bw ? xwm[k] : out[f].data, a_k, H, W, g.Ah, g.Aw, 0, 0, 0});
+                if (bw) post_warp.push_back(PostWarp{g, C, xwm[k], a_k, out[f].data});
             }
         }
     }
@@ -772,6 +807,12 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
         st = launch_tc(ctx, kTcFull, tf[1].data(), (int)tf[1].size(), 3, nullptr, nullptr, ctx->d_status, s);
     if (st == P2S_OK && !tf[0].empty())
         st = launch_tc(ctx, kTcFull, tf[0].data(), (int)tf[0].size(), 1, nullptr, nullptr, ctx->d_status, s);
+    for (const PostWarp &w : post_warp) {
+        if (st != P2S_OK) break;
+        const float *in1[1] = {w.in};
+        float *out1[1] = {w.out};
+        st = launch_warp(ctx, w.g, 1, in1, w.alpha, out1, w.C, s);
+    }
     sc.release();
     return st;
 }

@@ -114,6 +114,7 @@ struct p2s_ctx {
     // CUDA graphs of p2s_simulate (P2S_OPT_GRAPHS): scratch arena, internal
     // capture stream, instantiated graphs by batch signature
     int use_graphs = 0;
+    int blur_then_warp = 0;  // P2S_OPT_BLUR_THEN_WARP
     void *arena = nullptr;
     size_t arena_bytes = 0;
     cudaStream_t cap_stream = nullptr;

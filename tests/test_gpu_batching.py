@@ -127,3 +127,22 @@ def test_autotune_picks_a_candidate_and_keeps_results(form):
     sim.check()
     for u, v in zip(before, after):
         assert rel(v.cpu().numpy(), u.cpu().numpy()) < 1e-6
+
+
+@pytest.mark.parametrize("prec,form", [("fp16", "gather"), ("fp16", "scatter"), ("fp32", "scatter")])
+def test_blur_then_warp_order(prec, form):
+    """The collapsed model's order (Sec. 2.2): blur the input, then shift by the tilts."""
+    from gpu_common import TOL_FP32
+
+    sim = _sim(prec=prec, form=form)
+    sim.set_option("blur_then_warp", 1)
+    shapes = [(96, 160), (70, 130)]
+    xs = _frames(shapes, first=2300)
+    dr, seeds = [2.5, 5.0], [61, 62]
+    ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
+    sim.check()
+    tol = TOL_FP32 if prec == "fp32" else TOL_BF16
+    for i in range(2):
+        ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
+                                    CorrParams(8, (16.0,)), (33, 33), form=form, order="blur_warp")
+        assert rel(ys[i].cpu().numpy(), ref.y) < tol, (i, rel(ys[i].cpu().numpy(), ref.y))

@@ -47,3 +47,23 @@ def test_displacement_uses_tilt_modes():
     a[..., 1] = 2.0  # alpha_3 -> rows
     dr, dc = warp.displacement(a, -4 / np.pi)
     assert np.allclose(dc, -4 / np.pi) and np.allclose(dr, -8 / np.pi)
+
+
+def test_blur_and_integer_shift_commute_in_the_interior():
+    """Pin for the two orders of the path: with one shift-invariant PSF (constant beta) and a
+    constant integer shift, warp(blur(x)) == blur(warp(x)) away from the borders."""
+    from oracle import blur, warp
+
+    rng = np.random.default_rng(5)
+    h, w, K, T = 40, 44, 3, 5
+    x = rng.uniform(size=(h, w, 2))
+    Hb = rng.normal(size=(K, T * T))
+    beta = np.broadcast_to(rng.normal(size=K), (h, w, K)).copy()
+    kap = warp.kappa()
+    ap = np.zeros((h, w, 35))
+    ap[..., 0] = 3.0 / kap   # alpha_2 -> +3 columns
+    ap[..., 1] = -2.0 / kap  # alpha_3 -> -2 rows
+    a = warp.warp(blur.scatter(x, beta, Hb, T, T), ap, kap)
+    b = blur.scatter(warp.warp(x, ap, kap), beta, Hb, T, T)
+    m = 8
+    assert np.allclose(a[m:-m, m:-m], b[m:-m, m:-m], atol=1e-12)
