@@ -58,7 +58,8 @@ def _zernike_modes(js, n_pupil: int) -> np.ndarray:
 
 
 def psf_dictionary(n_dict: int, taps: int, n_pupil: int = 32, n_fft: int = 64, seed: int = 2021,
-                   dr0_range=(0.5, 6.0), chunk: int = 2000) -> np.ndarray:
+                   dr0_range=(0.5, 6.0), chunk: int = 2000, with_alpha: bool = False):
+    """[n_dict, taps*taps] unit-sum PSFs (and, with_alpha, the [n_dict, 35] coefficients alpha_2..36)."""
     z, dr0 = inputs.dictionary_draws(n_dict, 35, dr0_range, seed)
     L = np.linalg.cholesky(p2s.noll_covariance(36))
     alpha = (dr0[:, None] ** (5.0 / 6.0)) * (z @ L.T)
@@ -74,7 +75,8 @@ def psf_dictionary(n_dict: int, taps: int, n_pupil: int = 32, n_fft: int = 64, s
         h = np.fft.fftshift(np.abs(np.fft.fft2(pad)) ** 2, axes=(-2, -1))[:, h0:h0 + taps, h0:h0 + taps]
         h = h.reshape(h.shape[0], -1)
         rows.append(h / h.sum(axis=1, keepdims=True))
-    return np.concatenate(rows)
+    D = np.concatenate(rows)
+    return (D, alpha) if with_alpha else D
 
 
 def build_basis(K: int = 100, taps: int = 33, n_dict: int = 50_000, n_pupil: int = 32, n_fft: int = 64,
