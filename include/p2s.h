@@ -223,14 +223,20 @@ p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
  *   P2S_OPT_BLUR_THEN_WARP  1: p2s_simulate blurs the input first and applies
  *       the tilt warp to the blurred frame, the order of the collapsed model
  *       (Sec. 2.2: the turbulent PSF is a tilt-free PSF shifted by the tilt);
- *       0 (default): warp, then blur. */
+ *       0 (default): warp, then blur.
+ *   P2S_OPT_FIELD_METHOD  how the anchor fields get their spatial
+ *       correlation (Sec. 3.4): 0 (default) Fourier filtering on a torus;
+ *       1 the dense draw f = chol(Sigma) w of the anchors' full (unwrapped)
+ *       Gaussian correlation matrix, evaluated through its Kronecker factors
+ *       L_y W L_x^T (at most 128 anchors per axis). */
 typedef enum {
     P2S_OPT_SCATTER_SEGMENT_ROWS = 1,
     P2S_OPT_GRAPHS = 2,
     P2S_OPT_GRAPH_INSTANTIATIONS = 3,
     P2S_OPT_GRAPH_UPDATES = 4,
     P2S_OPT_GATHER_BAND_ROWS = 5,
-    P2S_OPT_BLUR_THEN_WARP = 6
+    P2S_OPT_BLUR_THEN_WARP = 6,
+    P2S_OPT_FIELD_METHOD = 7
 } p2s_option;
 p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value);
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value);

@@ -120,16 +120,47 @@ def filtered_fields(seed: int, h: int, w: int, p: CorrParams) -> np.ndarray:
     return out
 
 
+def gaussian_corr_1d(n: int, ell: float, s: int) -> np.ndarray:
+    """C[i, k] = exp(-((i - k) s)^2 / (2 ell^2)) over n anchors along one axis (not wrapped)."""
+    d = (np.arange(n)[:, None] - np.arange(n)[None, :]) * float(s)
+    return np.exp(-d * d / (2.0 * ell * ell))
+
+
+def dense_fields(seed: int, h: int, w: int, p: CorrParams) -> np.ndarray:
+    """The 35 unit-variance fields drawn directly from the anchors' correlation matrix (the
+    paper's dense anchor draw, Sec. 3.4): f_l = chol(Sigma) w_l over the A_h A_w anchors, with
+    Sigma[(a_y, a_x), (b_y, b_x)] = exp(-|a - b|^2 s^2 / (2 ell^2)) unwrapped.  That Gaussian
+    matrix is the Kronecker product C_y (x) C_x, whose Cholesky factor is L_y (x) L_x, so the
+    draw is evaluated as L_y W L_x^T with W the A_h x A_w white noise of stream (seed, mode),
+    samples taken row-major over the anchors.  [A_h, A_w, 35]."""
+    ah, aw = anchor_shape(h, w, p.anchor_spacing)
+    out = np.empty((ah, aw, N_MODES), dtype=np.float64)
+    Ls = {}
+    for l in range(N_MODES):
+        kk = p.kernel_of_mode(l + J_MIN)
+        if kk not in Ls:
+            ell = p.corr_len_px[kk]
+            Ls[kk] = (np.linalg.cholesky(gaussian_corr_1d(ah, ell, p.anchor_spacing)),
+                      np.linalg.cholesky(gaussian_corr_1d(aw, ell, p.anchor_spacing)))
+        Ly, Lx = Ls[kk]
+        wn = philox.normals(seed, l, ah * aw).reshape(ah, aw)
+        out[:, :, l] = Ly @ wn @ Lx.T
+    return out
+
+
 def colour(f: np.ndarray, d_over_r0: float, L: np.ndarray) -> np.ndarray:
     """alpha(a) = (D/r0)^(5/6) L f(a) for every anchor a."""
     return (float(d_over_r0) ** (5.0 / 6.0)) * np.einsum("jl,...l->...j", L, f)
 
 
-def alpha_anchors(seed: int, d_over_r0: float, h: int, w: int, p: CorrParams, L: np.ndarray | None = None) -> np.ndarray:
-    """Zernike coefficients J = 2..36 on the anchor grid: [A_h, A_w, 35]."""
+def alpha_anchors(seed: int, d_over_r0: float, h: int, w: int, p: CorrParams, L: np.ndarray | None = None,
+                  method: str = "fft") -> np.ndarray:
+    """Zernike coefficients J = 2..36 on the anchor grid: [A_h, A_w, 35].
+    method "fft": Fourier filtering on the torus; "dense": the direct draw of dense_fields."""
     if L is None:
         L = noll.cholesky_lower(noll.noll_cov(J_MAX))
-    return colour(filtered_fields(seed, h, w, p), d_over_r0, L)
+    f = filtered_fields(seed, h, w, p) if method == "fft" else dense_fields(seed, h, w, p)
+    return colour(f, d_over_r0, L)
 
 
 def alpha_pixels(alpha_a: np.ndarray, h: int, w: int, s: int) -> np.ndarray:

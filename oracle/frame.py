@@ -43,7 +43,7 @@ def mlp_emulated(v, layers, rnd):
 
 def simulate(x: np.ndarray, seed: int, d_over_r0: float, Hb: np.ndarray, layers, p: fields.CorrParams,
              taps: tuple[int, int], kap: float | None = None, form: str = "scatter", emulate: str | None = None,
-             L: np.ndarray | None = None, order: str = "warp_blur") -> Stages:
+             L: np.ndarray | None = None, order: str = "warp_blur", field_method: str = "fft") -> Stages:
     """The full path on one frame x [H, W, C] (float), FP64 throughout unless `emulate`.
 
     order "warp_blur": y = blur(warp(x)), the simulator's default; "blur_warp": y = warp(blur(x)),
@@ -54,7 +54,7 @@ def simulate(x: np.ndarray, seed: int, d_over_r0: float, Hb: np.ndarray, layers,
         L = noll.cholesky_lower(noll.noll_cov(36))
     if kap is None:
         kap = warp.kappa()
-    aa = fields.alpha_anchors(seed, d_over_r0, h, w, p, L)
+    aa = fields.alpha_anchors(seed, d_over_r0, h, w, p, L, method=field_method)
     ap = fields.alpha_pixels(aa, h, w, p.anchor_spacing)
     if order not in ("warp_blur", "blur_warp"):
         raise ValueError(order)
@@ -83,7 +83,7 @@ def exact_frame(x: np.ndarray, seed: int, d_over_r0: float, p: fields.CorrParams
         L = noll.cholesky_lower(noll.noll_cov(36))
     if kap is None:
         kap = warp.kappa(n_fft, n_pupil)
-    aa = fields.alpha_anchors(seed, d_over_r0, h, w, p, L)
+    aa = fields.alpha_anchors(seed, d_over_r0, h, w, p, L, method=field_method)
     ap = fields.alpha_pixels(aa, h, w, p.anchor_spacing)
     xw = warp.warp(x, ap, kap)
     hp = psf.psf_taps(ap[..., 2:], taps[0], taps[1], n_pupil, n_fft)

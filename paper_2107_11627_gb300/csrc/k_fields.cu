@@ -10,6 +10,9 @@
 // column pass that the anchors use are kept.
 #include <stdint.h>
 
+#include <cmath>
+#include <vector>
+
 #include "fft_smem.cuh"
 #include "p2s_internal.h"
 
@@ -221,9 +224,128 @@ size_t fields_scratch_bytes(const FieldGeom &g, int n) {
     return ((t + 255) & ~(size_t)255) + f;
 }
 
+// Dense anchor draw (Sec. 3.4): f = chol(Sigma) w over the anchors, Sigma the
+// unwrapped Gaussian correlation, evaluated through its Kronecker factors as
+// f = L_y W L_x^T (W: white noise of stream (seed, mode) row-major over the
+// anchors).  One CTA per (mode, frame); W and L_y W in shared memory.
+__global__ void __launch_bounds__(kThreads) dense_field_kernel(FrameBatch fb, int Ah, int Aw,
+                                                               const float *__restrict__ Ly,
+                                                               const float *__restrict__ Lx,
+                                                               const int *__restrict__ kernel_of_mode, float *f) {
+    extern __shared__ float sdf[];
+    const int mode = blockIdx.x, frame = blockIdx.y;
+    const int A = Ah * Aw;
+    float *W = sdf, *T = sdf + A;
+    const unsigned long long seed = fb.seed[frame];
+    for (int q = threadIdx.x; 4 * q < A; q += blockDim.x) {
+        float z[4];
+        normals4(seed, mode, (uint32_t)q, z);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (4 * q + i < A) W[4 * q + i] = z[i];
+    }
+    __syncthreads();
+    const int kk = kernel_of_mode[mode];
+    const float *ly = Ly + (size_t)kk * Ah * Ah, *lx = Lx + (size_t)kk * Aw * Aw;
+    for (int e = threadIdx.x; e < A; e += blockDim.x) {  // T = L_y W (L_y lower triangular)
+        const int i = e / Aw, j = e - i * Aw;
+        float acc = 0.f;
+        for (int k = 0; k <= i; ++k) acc = fmaf(__ldg(ly + (size_t)i * Ah + k), W[k * Aw + j], acc);
+        T[e] = acc;
+    }
+    __syncthreads();
+    float *ff = f + ((size_t)frame * kModes + mode) * A;
+    for (int e = threadIdx.x; e < A; e += blockDim.x) {  // F = T L_x^T
+        const int i = e / Aw, j = e - i * Aw;
+        float acc = 0.f;
+        for (int m = 0; m <= j; ++m) acc = fmaf(T[i * Aw + m], __ldg(lx + (size_t)j * Aw + m), acc);
+        ff[e] = acc;
+    }
+}
+
+// lower Cholesky factor (FP32) of the 1-D unwrapped Gaussian correlation over
+// n anchors for every kernel, [n_kernels][n][n], built in FP64 on the host
+static p2s_status dense_factor(p2s_ctx *ctx, int n, const float **out) {
+    auto it = ctx->dense_L.find(n);
+    if (it != ctx->dense_L.end()) {
+        *out = (const float *)it->second;
+        return P2S_OK;
+    }
+    std::vector<float> Lf((size_t)ctx->n_kernels * n * n, 0.f);
+    std::vector<double> C((size_t)n * n);
+    for (int kk = 0; kk < ctx->n_kernels; ++kk) {
+        const double ell = ctx->ell[kk], s = ctx->s;
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < n; ++k) {
+                const double d = (i - k) * s;
+                C[(size_t)i * n + k] = std::exp(-d * d / (2.0 * ell * ell));
+            }
+        // Cholesky-Banachiewicz, row by row
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k <= i; ++k) {
+                double acc = C[(size_t)i * n + k];
+                for (int m = 0; m < k; ++m) acc -= C[(size_t)i * n + m] * C[(size_t)k * n + m];
+                if (i == k) {
+                    if (acc <= 0.0) {
+                        set_error("anchor correlation matrix of %d points is not positive definite (ell / spacing too "
+                                  "large for the dense draw)", n);
+                        return P2S_EINVAL;
+                    }
+                    C[(size_t)i * n + i] = std::sqrt(acc);
+                } else {
+                    C[(size_t)i * n + k] = acc / C[(size_t)k * n + k];
+                }
+            }
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k <= i; ++k) Lf[((size_t)kk * n + i) * n + k] = (float)C[(size_t)i * n + k];
+    }
+    void *d = nullptr;
+    if (cudaMalloc(&d, Lf.size() * sizeof(float)) != cudaSuccess) {
+        set_error("no memory for the dense-draw factors");
+        return P2S_ENOMEM;
+    }
+    P2S_CUDA(cudaMemcpy(d, Lf.data(), Lf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    ctx->dense_L[n] = d;
+    *out = (const float *)d;
+    return P2S_OK;
+}
+
+p2s_status dense_prepare(p2s_ctx *ctx, const FieldGeom &g) {
+    const float *a, *b;
+    p2s_status s = dense_factor(ctx, g.Ah, &a);
+    return s == P2S_OK ? dense_factor(ctx, g.Aw, &b) : s;
+}
+
 p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb, float *alpha, void *scratch,
                          cudaStream_t st) {
     if (fb.n <= 0) return P2S_OK;
+    if (ctx->field_method == 1) {
+        if (g.Ah > 128 || g.Aw > 128) {
+            set_error("the dense anchor draw supports at most 128 anchors per axis");
+            return P2S_EUNSUPPORTED;
+        }
+        const float *Ly = nullptr, *Lx = nullptr;
+        p2s_status s0 = dense_factor(ctx, g.Ah, &Ly);
+        if (s0 == P2S_OK) s0 = dense_factor(ctx, g.Aw, &Lx);
+        if (s0 != P2S_OK) return s0;
+        const size_t t_bytes = (size_t)fb.n * kModes * g.Fh * g.Aw * sizeof(float);
+        float *f = (float *)((char *)scratch + ((t_bytes + 255) & ~(size_t)255));
+        const int A = g.Ah * g.Aw;
+        const size_t smem = (size_t)2 * A * sizeof(float);
+        P2S_CUDA(cudaFuncSetAttribute(dense_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        {
+            ProfScope pd(ctx, st, "fields_dense", (double)fb.n * kModes * A * (g.Ah + g.Aw), (double)fb.n * kModes * A * 4);
+            dense_field_kernel<<<dim3(kModes, fb.n), kThreads, smem, st>>>(fb, g.Ah, g.Aw, Ly, Lx,
+                                                                           ctx->d_kernel_of_mode, f);
+            P2S_CUDA(cudaGetLastError());
+        }
+        dim3 grid_a((A + 127) / 128, fb.n);
+        ProfScope pa(ctx, st, "fields_colour", (double)fb.n * A * kModes * (kModes + 1),
+                     (double)fb.n * A * (kModes + kAlphaStride) * 4);
+        colour_kernel<<<grid_a, 128, 0, st>>>(fb, A, ctx->d_L, f, alpha);
+        P2S_CUDA(cudaGetLastError());
+        return P2S_OK;
+    }
     const FilterTable *th = nullptr, *tw = nullptr;
     p2s_status s = filter_table(ctx, g.Fh, &th);
     if (s != P2S_OK) return s;

@@ -357,6 +357,7 @@ void p2s_destroy(p2s_ctx *ctx) {
     cudaFree(ctx->tc.d_bias);
     cudaFree(ctx->tc.d_Hs);
     for (auto &kv : ctx->fft_tw) cudaFree(kv.second);
+    for (auto &kv : ctx->dense_L) cudaFree(kv.second);
     for (auto &kv : ctx->fft_basis) cudaFree(kv.second);
     for (auto &kv : ctx->graphs)
         if (kv.second) cudaGraphExecDestroy(kv.second);
@@ -539,6 +540,11 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
         ctx->blur_then_warp = value;
         return P2S_OK;
     }
+    if (option == P2S_OPT_FIELD_METHOD) {
+        if (value != 0 && value != 1) return einval("field method is 0 (Fourier filtering) or 1 (dense draw)");
+        ctx->field_method = value;
+        return P2S_OK;
+    }
     return einval("unknown option");
 }
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
@@ -565,6 +571,10 @@ p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
     }
     if (option == P2S_OPT_BLUR_THEN_WARP) {
         *value = ctx->blur_then_warp;
+        return P2S_OK;
+    }
+    if (option == P2S_OPT_FIELD_METHOD) {
+        *value = ctx->field_method;
         return P2S_OK;
     }
     return einval("unknown option");
@@ -884,6 +894,7 @@ static p2s_status simulate_graph(p2s_ctx *ctx, const p2s_image *frames, int n, c
         const FilterTable *t;
         if ((st = geometry(ctx, frames[i].H, frames[i].W, &g)) != P2S_OK) return st;
         if ((st = filter_table(ctx, g.Fh, &t)) != P2S_OK || (st = filter_table(ctx, g.Fw, &t)) != P2S_OK) return st;
+        if (ctx->field_method == 1 && (st = dense_prepare(ctx, g)) != P2S_OK) return st;
     }
     std::string key;
     for (int i = 0; i < n; ++i) {

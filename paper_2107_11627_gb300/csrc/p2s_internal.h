@@ -115,6 +115,8 @@ struct p2s_ctx {
     // capture stream, instantiated graphs by batch signature
     int use_graphs = 0;
     int blur_then_warp = 0;  // P2S_OPT_BLUR_THEN_WARP
+    int field_method = 0;    // P2S_OPT_FIELD_METHOD: 0 Fourier filtering, 1 dense draw
+    std::map<int, void *> dense_L;  // dense draw: FP32 Cholesky factors [n_kernels][n][n] by n
     void *arena = nullptr;
     size_t arena_bytes = 0;
     cudaStream_t cap_stream = nullptr;
@@ -192,5 +194,6 @@ int scatter_segment_rows(const p2s_ctx *ctx, int H);
 p2s_status launch_blur_fft(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, const float *beta,
                            float *const *y, cudaStream_t st);
 p2s_status scatter_prepare(p2s_ctx *ctx);
+p2s_status dense_prepare(p2s_ctx *ctx, const FieldGeom &g);
 
 }  // namespace p2s

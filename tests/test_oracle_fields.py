@@ -92,3 +92,44 @@ def test_bilinear_interpolation():
     assert np.allclose(ap[::s, ::s], aa[:4, :5])
     assert np.allclose(ap[2, 0], 0.5 * (aa[0, 0] + aa[1, 0]))
     assert np.allclose(ap[1, 3], (3 / 4) * ((1 / 4) * aa[0, 0] + (3 / 4) * aa[0, 1]) + (1 / 4) * ((1 / 4) * aa[1, 0] + (3 / 4) * aa[1, 1]))
+
+
+def test_dense_draw_equals_explicit_cholesky_of_the_full_matrix():
+    """The separable evaluation L_y W L_x^T is the draw chol(Sigma) vec(W) of the full
+    A_h A_w x A_h A_w anchor correlation matrix (built and factored explicitly here)."""
+    from oracle import fields, philox
+
+    p = fields.CorrParams(8, (16.0,))
+    h, w = 33, 41  # 6 x 7 anchors
+    ah, aw = fields.anchor_shape(h, w, 8)
+    ys, xs = np.meshgrid(np.arange(ah), np.arange(aw), indexing="ij")
+    pts = np.stack([ys.ravel(), xs.ravel()], axis=1) * 8.0
+    d2 = ((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1)
+    S = np.exp(-d2 / (2 * 16.0 ** 2))
+    Lfull = np.linalg.cholesky(S)
+    f = fields.dense_fields(99, h, w, p)
+    for l in (0, 17, 34):
+        wn = philox.normals(99, l, ah * aw)
+        np.testing.assert_allclose(f[:, :, l].ravel(), Lfull @ wn, rtol=0, atol=1e-10)
+
+
+def test_dense_draw_covariance_matches_target():
+    """Sample covariance over many seeds: Cov(alpha_i(a), alpha_j(b)) = (D/r0)^(5/3) R_Z[i,j] Sigma[a,b]."""
+    from oracle import fields, noll
+
+    p = fields.CorrParams(8, (16.0,))
+    R = noll.noll_cov(36)  # J = 2..36
+    L = noll.cholesky_lower(noll.noll_cov(36))
+    h = w = 17  # 4 x 4 anchors
+    n = 2000
+    dr = 2.0
+    a = np.stack([fields.alpha_anchors(5000 + k, dr, h, w, p, L, method="dense") for k in range(n)])
+    # anchors (0, 0) and (0, 1): spatial correlation exp(-64 / 512)
+    c01 = np.exp(-64.0 / (2 * 256.0))
+    for i, j in ((0, 0), (0, 6), (2, 9), (1, 1)):
+        for (ay, ax, by, bx, c) in ((0, 0, 0, 0, 1.0), (0, 0, 0, 1, c01)):
+            target = dr ** (5 / 3) * R[i, j] * c
+            x, y = a[:, ay, ax, i], a[:, by, bx, j]
+            est = np.mean(x * y)
+            se = np.sqrt((np.var(x) * np.var(y) + est ** 2) / n)
+            assert abs(est - target) < 5 * se + 1e-12, (i, j, ay, ax, by, bx, est, target, se)
