@@ -129,6 +129,21 @@ def test_frame_cfg2_batch_and_invariance():
     assert sim.simulate([], [], []) == []
 
 
+def test_frame_cfg2_full_size_batch():
+    """The 256 x 256 RGB, 16-frame FP32 workload in one call; frames 0 and 11 checked whole."""
+    cfg = cfg2()
+    sim = _sim(cfg)
+    n = 16
+    xs = inputs.blob_batch(n, 256, 256, 3, 1000)
+    dr = inputs.frame_strengths(n, 1.0, 5.0, 7)
+    seeds = inputs.frame_seeds(n)
+    ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
+    for i in (0, 11):
+        ref = oracle.frame.simulate(xs[i].astype(np.float64), int(seeds[i]), float(dr[i]), cfg["H"], cfg["layers"],
+                                    CorrParams(8, (16.0,)), cfg["taps"])
+        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_FP32, (i, rel(ys[i].cpu().numpy(), ref.y))
+
+
 def test_host_entry_point_matches_device():
     cfg = cfg1()
     sim = _sim(cfg)
