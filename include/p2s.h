@@ -228,7 +228,15 @@ p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
  *       correlation (Sec. 3.4): 0 (default) Fourier filtering on a torus;
  *       1 the dense draw f = chol(Sigma) w of the anchors' full (unwrapped)
  *       Gaussian correlation matrix, evaluated through its Kronecker factors
- *       L_y W L_x^T (at most 128 anchors per axis). */
+ *       L_y W L_x^T (at most 128 anchors per axis).
+ *   P2S_OPT_GATHER_SPLIT  tensor-core gather form only.  0 (default): one
+ *       fused kernel evaluates the network and the blur per tile, beta never
+ *       leaves the SM.  1: the network kernel writes beta in its 16-bit
+ *       operand layout (224 B per pixel) and a blur-only tensor-core kernel
+ *       with three accumulating warps per TMEM lane quadrant reads it back.
+ *       Same rounding points (beta and H in 16 bits, x staged in FP16, FP32
+ *       accumulation); results differ from the fused kernel only in the order
+ *       of FP32 summation. */
 typedef enum {
     P2S_OPT_SCATTER_SEGMENT_ROWS = 1,
     P2S_OPT_GRAPHS = 2,
@@ -236,16 +244,17 @@ typedef enum {
     P2S_OPT_GRAPH_UPDATES = 4,
     P2S_OPT_GATHER_BAND_ROWS = 5,
     P2S_OPT_BLUR_THEN_WARP = 6,
-    P2S_OPT_FIELD_METHOD = 7
+    P2S_OPT_FIELD_METHOD = 7,
+    P2S_OPT_GATHER_SPLIT = 8
 } p2s_option;
 p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value);
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value);
 
 /* Autotuner (no counterpart in the paper).  Runs p2s_simulate on the given
  * batch (device frames, written to `out`) once per candidate setting of the
- * tile-shape option of the context's path (P2S_OPT_GATHER_BAND_ROWS for the
- * tensor-core gather, P2S_OPT_SCATTER_SEGMENT_ROWS for the tensor-core
- * scatter; the FP32 path has none), after one warm-up call times `reps`
+ * launch option of the context's path (P2S_OPT_GATHER_SPLIT, fused or split
+ * kernels, for the tensor-core gather; P2S_OPT_SCATTER_SEGMENT_ROWS for the
+ * tensor-core scatter; the FP32 path has none), after one warm-up call times `reps`
  * calls with CUDA events on `stream` (synchronising it), keeps the fastest
  * setting in the context and reports every candidate in `res` (may be NULL).
  * Arguments as p2s_simulate; reps >= 1. */

@@ -1,0 +1,470 @@
+// Blur-only tensor-core gather (Sec. 3.1, Eq. 5) reading beta from the
+// network kernel's 16-bit operand layout: the split alternative to the fused
+// kernel, chosen by P2S_OPT_GATHER_SPLIT.
+//
+// With the network out of the kernel, the tap accumulation gets three warps
+// per TMEM lane quadrant (12 accumulating warps) instead of two: each takes a
+// third of the tap rows of every chunk, with its own window of x.  Per row
+// pair of a 128 x 32 tile:
+//   producer  beta rows (2 x 14 runs of 16-byte groups) into a staging buffer
+//             with 1-D bulk copies, basis chunks into a 2-slot ring;
+//   warps of groups 0, 1 move their row's beta from the staging buffer into
+//             TMEM (the A operand), then everyone accumulates;
+//   MMA       G = beta H chunk by chunk (N = 96: 3 tap columns x 32 tap rows,
+//             then N = 48 for the last tap row), two TMEM buffers;
+//   gather    y_c[q] += G[q, t] x_c[q - o(t)], x staged as FP16 RGB, FP32
+//             accumulation; the three groups' partial sums are added through
+//             shared memory and written.
+// Every wait is bounded.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstring>
+
+#include "p2s_internal.h"
+#include "tc_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace p2s {
+namespace gs {
+
+using tcc::Ctl;
+using tcc::drain_bar;
+using tcc::wait_bar;
+
+constexpr int kStrip = 128;
+constexpr int kBand = 32;
+constexpr int kHalo = 16;
+constexpr int kTR = kBand + 2 * kHalo;
+constexpr int kTC = kStrip + 2 * kHalo;
+constexpr int kKSteps = 7;
+constexpr int kMainN = 96;
+constexpr int kMainChunks = 11;
+constexpr int kChunks = kMainChunks + 1;
+constexpr int kSlot = 32768;
+constexpr int kSlots = 2;
+constexpr int kGroups = 14;                       // beta16 k-groups
+constexpr int kGroupsEpi = 3;                     // accumulating groups of 4 warps
+constexpr int kEpi = 128 * kGroupsEpi;            // 384
+constexpr int kThreads = 64 + kEpi;               // 448
+constexpr int kBetaRow = kGroups * kStrip * 16;   // 28,672 B per staged row
+
+__host__ __device__ constexpr uint32_t colBeta(int r) { return r ? 56u : 0u; }
+__host__ __device__ constexpr uint32_t colDB(int h) { return h ? 320u : 128u; }
+
+constexpr int kOffRing = 0;
+constexpr int kOffX = kOffRing + kSlots * kSlot;           // uint2 [kTR][kTC]
+constexpr int kOffBeta = kOffX + kTR * kTC * 8;            // [2 rows][14][128][16 B]
+constexpr int kOffXchg = kOffBeta + 2 * kBetaRow;          // float [2][128][6]
+enum Bar { kFull0 = 0, kEmpty0 = 2, kBStaged = 4, kBFree = 5, kBReady = 6, kDFull0 = 7, kDEmpty0 = 9, kNBar = 11 };
+constexpr int kOffBar = kOffXchg + 2 * kStrip * 6 * 4;
+constexpr int kOffMisc = kOffBar + kNBar * 8;
+constexpr int kSmemBytes = kOffMisc + 16 + 1024;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+
+struct Item {
+    uint32_t offset, bytes, n, k;
+};
+
+struct Frame {
+    const float *xw;
+    float *y;
+    const uint4 *beta16;  // [H][14][W] 16-byte groups
+    int H, W, tiles_x, tiles_y, tile_base;
+};
+constexpr int kMaxFrames = 256;
+
+struct Params {
+    Frame fr[kMaxFrames];
+    int n_frames, tiles_total;
+    const uint8_t *stream;  // basis chunk images
+    Item item[kChunks];
+    int ab_fmt;
+    int *status;
+};
+static_assert(sizeof(Params) <= 32000, "kernel parameter block");
+
+__device__ __forceinline__ int frame_of(const Params &p, int tile) {
+    int lo = 0, hi = p.n_frames - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.fr[mid].tile_base <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// tap rows of group g in a main chunk: [11 g, 11 g + n), n = 11, 11, 10
+__host__ __device__ constexpr int grp_r0(int g) { return 11 * g; }
+__host__ __device__ constexpr int grp_n(int g) { return g == 2 ? 10 : 11; }
+// first TMEM column of a group's 16-column load inside a 32-column tap column
+// (kept inside the block so the second buffer's last load ends at column 512)
+__host__ __device__ constexpr int grp_ls(int g) { return g == 2 ? 16 : 11 * g; }
+static_assert(grp_ls(2) + 16 <= 32 && grp_r0(2) - grp_ls(2) + grp_n(2) <= 16, "group 2 load window");
+
+// One staged pixel of x: (R, G) and (B, 0) as FP16 pairs, 8 bytes.
+__device__ __forceinline__ uint2 encode_px(float r, float g, float b) {
+    const __half2 rg = __floats2half2_rn(r, g), b0 = __floats2half2_rn(b, 0.f);
+    return make_uint2(*reinterpret_cast<const uint32_t *>(&rg), *reinterpret_cast<const uint32_t *>(&b0));
+}
+
+template <int C>
+__device__ __forceinline__ void decode_px(uint2 v, float &r, float &g, float &b) {
+    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+    r = rg.x;
+    g = (C == 3) ? rg.y : 0.f;
+    b = (C == 3) ? __low2float(*reinterpret_cast<const __half2 *>(&v.y)) : 0.f;
+}
+
+template <int C, int G>
+__device__ __forceinline__ void accumulate_pair(const Params &p, const uint2 *x16, uint32_t lane_base, int col, int rp,
+                                                uint32_t bar0, uint32_t &uses, bool &ok, const Ctl &ctl, int lane,
+                                                float (&acc)[2][3]) {
+    constexpr int R0 = grp_r0(G), NT = grp_n(G), NW = NT + 1, LS = grp_ls(G), OFF = R0 - LS;
+    auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    const int wbase = 2 * rp + 33 - R0 - NT;  // first window row of this group
+    const uint2 *xw0 = x16 + wbase * kTC + col + 32;  // window of tap column txx starts at xw0 - txx
+    for (int c = 0; c < kChunks; ++c) {
+        const int b = c & 1;
+        const uint32_t buf = lane_base + colDB(b);
+        const bool got = __all_sync(0xffffffffu, wait_bar(BAR(kDFull0 + b), (uses >> b) & 1, ctl, 128));
+        uses ^= (1u << b);
+        ok = ok && got;
+        ptx::fence_after();
+        if (!got) {
+        } else if (c < kMainChunks) {
+#pragma unroll 1
+            for (int u3 = 0; u3 < 3; ++u3) {
+                // G of this tap column (loading the next one ahead would keep two copies
+                // live across the loop: register moves for every tap)
+                uint32_t g0[16], g1[16];
+                ptx::tmem_ld16(buf + 32 * u3 + LS, g0);
+                ptx::tmem_ld16(buf + kMainN + 32 * u3 + LS, g1);
+                const int txx = 3 * c + u3;
+                float wr[NW], wg[NW], wb[NW];
+#pragma unroll
+                for (int m = 0; m < NW; ++m) decode_px<C>(xw0[m * kTC - txx], wr[m], wg[m], wb[m]);
+                ptx::tmem_wait_ld_dep(g0);
+                ptx::tmem_wait_ld_dep(g1);
+                float a[NT], bb[NT];
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    a[t] = __uint_as_float(g0[OFF + t]);
+                    bb[t] = __uint_as_float(g1[OFF + t]);
+                }
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    // tap row R0 + t: window rows NT - 1 - t (row 0) and NT - t (row 1)
+                    acc[0][0] = fmaf(a[t], wr[NT - 1 - t], acc[0][0]);
+                    acc[1][0] = fmaf(bb[t], wr[NT - t], acc[1][0]);
+                    if (C == 3) {
+                        acc[0][1] = fmaf(a[t], wg[NT - 1 - t], acc[0][1]);
+                        acc[0][2] = fmaf(a[t], wb[NT - 1 - t], acc[0][2]);
+                        acc[1][1] = fmaf(bb[t], wg[NT - t], acc[1][1]);
+                        acc[1][2] = fmaf(bb[t], wb[NT - t], acc[1][2]);
+                    }
+                }
+            }
+        } else {
+            // last tap row (tap row 32): tap columns [11 G, 11 G + 11), window rows 2 rp + i
+            uint32_t g0[16], g1[16];
+            ptx::tmem_ld16(buf + 11 * G, g0);
+            ptx::tmem_ld16(buf + kMainN + 11 * G, g1);
+            ptx::tmem_wait_ld_dep(g0);
+            ptx::tmem_wait_ld_dep(g1);
+#pragma unroll
+            for (int q = 0; q < 11; ++q) {
+                const int txx = 11 * G + q;
+                const int i0 = (2 * rp) * kTC + col + 32 - txx, i1 = i0 + kTC;
+                const float a = __uint_as_float(g0[q]), b2 = __uint_as_float(g1[q]);
+                float r0, gg0, b0, r1, gg1, b1;
+                decode_px<C>(x16[i0], r0, gg0, b0);
+                decode_px<C>(x16[i1], r1, gg1, b1);
+                acc[0][0] = fmaf(a, r0, acc[0][0]);
+                acc[1][0] = fmaf(b2, r1, acc[1][0]);
+                if (C == 3) {
+                    acc[0][1] = fmaf(a, gg0, acc[0][1]);
+                    acc[0][2] = fmaf(a, b0, acc[0][2]);
+                    acc[1][1] = fmaf(b2, gg1, acc[1][1]);
+                    acc[1][2] = fmaf(b2, b1, acc[1][2]);
+                }
+            }
+        }
+        ptx::fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(BAR(kDEmpty0 + b));
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_constant__ Params p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = ptx::smem_u32(sm);
+    uint2 *x16 = (uint2 *)(sm + kOffX);
+    const uint4 *sbeta = (const uint4 *)(sm + kOffBeta);
+    float *xchg = (float *)(sm + kOffXchg);
+    const uint32_t bar0 = sbase + kOffBar;
+    uint32_t *tmem_holder = (uint32_t *)(sm + kOffMisc);
+    volatile int *abort_flag = (volatile int *)(sm + kOffMisc + 4);
+    auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Ctl ctl{abort_flag, p.status};
+
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        for (int i = 0; i < kSlots; ++i) {
+            ptx::mbar_init(BAR(kFull0 + i), 1);
+            ptx::mbar_init(BAR(kEmpty0 + i), 1);
+        }
+        ptx::mbar_init(BAR(kBStaged), 1);
+        ptx::mbar_init(BAR(kBFree), 8);
+        ptx::mbar_init(BAR(kBReady), 8);
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(BAR(kDFull0 + i), 1);
+            ptx::mbar_init(BAR(kDEmpty0 + i), 4 * kGroupsEpi);
+        }
+        ptx::mbar_fence_init();
+    }
+    if (warp == 0) ptx::tmem_alloc(ptx::smem_u32(tmem_holder), 512);
+    ptx::fence_before();
+    __syncthreads();
+    ptx::fence_after();
+    const uint32_t tmem = *tmem_holder;
+    const uint32_t idesc_n96 = ptx::idesc_f16(p.ab_fmt, kMainN);
+    const uint32_t idesc_n48 = ptx::idesc_f16(p.ab_fmt, 48);
+
+    auto n_pairs_of = [&](int tile) {
+        const Frame &F = p.fr[frame_of(p, tile)];
+        const int ty = (tile - F.tile_base) / F.tiles_x;
+        return (min(kBand, F.H - ty * kBand) + 1) >> 1;
+    };
+
+    if (warp == 1) {
+        // ---------------- producer: beta rows, basis chunks ----------------
+        if (lane == 0) {
+            uint32_t it = 0, pairs = 0;
+            for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
+                const int f = frame_of(p, tile);
+                const Frame &F = p.fr[f];
+                const int lt = tile - F.tile_base;
+                const int tyy = lt / F.tiles_x, c0 = (lt - tyy * F.tiles_x) * kStrip;
+                const int npair = n_pairs_of(tile);
+                const uint32_t cols = (uint32_t)min(kStrip, F.W - c0);
+                for (int rp = 0; rp < npair; ++rp, ++pairs) {
+                    // beta of the pair's rows; the staging buffer is free once both rows are in TMEM
+                    if (wait_bar(BAR(kBFree), (pairs & 1) ^ 1, ctl, 1)) {
+                        const int r0 = tyy * kBand + 2 * rp;
+                        const int nrow = min(2, F.H - r0);
+                        ptx::mbar_arrive_tx(BAR(kBStaged), (uint32_t)nrow * kGroups * cols * 16);
+                        for (int i = 0; i < nrow; ++i)
+                            for (int g = 0; g < kGroups; ++g)
+                                ptx::bulk_g2s(sbase + kOffBeta + i * kBetaRow + g * kStrip * 16,
+                                              F.beta16 + ((size_t)(r0 + i) * kGroups + g) * F.W + c0, cols * 16,
+                                              BAR(kBStaged));
+                    }
+                    for (int c = 0; c < kChunks; ++c, ++it) {
+                        const Item itm = p.item[c];
+                        const uint32_t slot = it % kSlots;
+                        if (!wait_bar(BAR(kEmpty0 + slot), ((it / kSlots) & 1) ^ 1, ctl, 2)) continue;
+                        ptx::mbar_arrive_tx(BAR(kFull0 + slot), itm.bytes);
+                        ptx::bulk_g2s(sbase + kOffRing + slot * kSlot, p.stream + itm.offset, itm.bytes, BAR(kFull0 + slot));
+                    }
+                }
+            }
+            for (uint32_t k = (it > (uint32_t)kSlots ? it - kSlots : 0); k < it; ++k)
+                drain_bar(BAR(kFull0 + k % kSlots), (k / kSlots) & 1);
+            if (pairs > 0) drain_bar(BAR(kBStaged), (pairs - 1) & 1);
+        }
+    } else if (warp == 0) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t it = 0, pairs = 0, uses[2] = {0, 0};
+            for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
+                const int npair = n_pairs_of(tile);
+                for (int rp = 0; rp < npair; ++rp, ++pairs) {
+                    const bool brdy = wait_bar(BAR(kBReady), pairs & 1, ctl, 8);
+                    ptx::fence_after();
+                    for (int c = 0; c < kChunks; ++c, ++it) {
+                        const int h = c & 1;
+                        const uint32_t slot = it % kSlots;
+                        const bool full = wait_bar(BAR(kFull0 + slot), (it / kSlots) & 1, ctl, 2);
+                        const bool free_buf = wait_bar(BAR(kDEmpty0 + h), (uses[h] & 1) ^ 1, ctl, 16);
+                        ptx::fence_after();
+                        if (brdy && full && free_buf) {
+                            const uint32_t n = p.item[c].n;
+                            const uint32_t idesc = (n == (uint32_t)kMainN) ? idesc_n96 : idesc_n48;
+                            const uint64_t bd = ptx::smem_desc(sbase + kOffRing + slot * kSlot, n * 16, 128);
+                            const uint64_t bstep = (uint64_t)(2 * n);
+                            const uint32_t d0 = tmem + colDB(h), d1 = d0 + kMainN;
+                            const uint32_t a0 = tmem + colBeta(0), a1 = tmem + colBeta(1);
+#pragma unroll
+                            for (int ks = 0; ks < kKSteps; ++ks) {
+                                ptx::mma_ts(d0, a0 + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
+                                ptx::mma_ts(d1, a1 + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
+                            }
+                        }
+                        ptx::mma_commit(BAR(kEmpty0 + slot));
+                        ptx::mma_commit(BAR(kDFull0 + h));
+                        ++uses[h];
+                    }
+                }
+            }
+        }
+    } else {
+        // ---------------- 12 accumulating warps: three per TMEM lane quadrant ----------------
+        const int e = warp - 2;
+        const int grp = e >> 2;
+        const int quad = warp & 3;
+        const int col = quad * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        const int tid_e = threadIdx.x - 64;
+        uint32_t pairs = 0, uses = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
+            const int f = frame_of(p, tile);
+            const Frame &F = p.fr[f];
+            const int lt = tile - F.tile_base;
+            const int tyy = lt / F.tiles_x, txx = lt - tyy * F.tiles_x;
+            const int r_band = tyy * kBand, c0 = txx * kStrip;
+            const int npair = n_pairs_of(tile);
+            ptx::named_bar(1, kEpi);  // previous tile fully consumed
+            for (int i = tid_e; i < kTR * kTC; i += kEpi) {
+                const int tr = i / kTC, tcol = i - tr * kTC;
+                const int gr = r_band - kHalo + tr, gc = c0 - kHalo + tcol;
+                float r = 0.f, g = 0.f, b = 0.f;
+                if (gr >= 0 && gr < F.H && gc >= 0 && gc < F.W) {
+                    const float *px = F.xw + ((size_t)gr * F.W + gc) * C;
+                    r = __ldg(px);
+                    if (C == 3) {
+                        g = __ldg(px + 1);
+                        b = __ldg(px + 2);
+                    }
+                }
+                x16[i] = encode_px(r, g, b);
+            }
+            ptx::named_bar(1, kEpi);
+            for (int rp = 0; rp < npair; ++rp, ++pairs) {
+                // ---- beta of row 2 rp + grp into TMEM (groups 0 and 1) ----
+                if (grp < 2) {
+                    ok = __all_sync(0xffffffffu, wait_bar(BAR(kBStaged), pairs & 1, ctl, 32) && ok);
+                    if (ok) {
+                        const uint4 *src = sbeta + grp * (kBetaRow / 16) + col;
+#pragma unroll
+                        for (int q = 0; q < kGroups / 2; ++q) {
+                            const uint4 v0 = src[(2 * q) * kStrip], v1 = src[(2 * q + 1) * kStrip];
+                            const uint32_t u[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                            ptx::tmem_st8(lane_base + colBeta(grp) + 8 * q, u);
+                        }
+                        ptx::tmem_wait_st();
+                    }
+                    ptx::fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        ptx::mbar_arrive(BAR(kBFree));
+                        ptx::mbar_arrive(BAR(kBReady));
+                    }
+                }
+                float acc[2][3];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) acc[i][ch] = 0.f;
+                if (grp == 0)
+                    accumulate_pair<C, 0>(p, x16, lane_base, col, rp, bar0, uses, ok, ctl, lane, acc);
+                else if (grp == 1)
+                    accumulate_pair<C, 1>(p, x16, lane_base, col, rp, bar0, uses, ok, ctl, lane, acc);
+                else
+                    accumulate_pair<C, 2>(p, x16, lane_base, col, rp, bar0, uses, ok, ctl, lane, acc);
+                // ---- add the three groups' partial sums, write the row pair ----
+                if (grp > 0) {
+                    float *xc = xchg + (grp - 1) * kStrip * 6;
+#pragma unroll
+                    for (int i = 0; i < 2; ++i)
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) xc[col * 6 + i * 3 + ch] = acc[i][ch];
+                }
+                ptx::named_bar(2, kEpi);
+                if (grp == 0 && ok) {
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int orow = r_band + 2 * rp + i;
+                        if (orow < F.H && c0 + col < F.W) {
+                            float *o = F.y + ((size_t)orow * F.W + c0 + col) * C;
+#pragma unroll
+                            for (int ch = 0; ch < C; ++ch)
+                                o[ch] = acc[i][ch] + xchg[col * 6 + i * 3 + ch] + xchg[kStrip * 6 + col * 6 + i * 3 + ch];
+                        }
+                    }
+                }
+                ptx::named_bar(2, kEpi);
+            }
+        }
+    }
+    // ---------------- teardown ----------------
+    ptx::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        ptx::fence_after();
+        ptx::tmem_dealloc(tmem, 512);
+    }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+p2s_status launch_gather_split(p2s_ctx *ctx, const TcFrame *frames, const void *const *beta16, int n, int C,
+                               int *status, cudaStream_t st) {
+    if (n <= 0) return P2S_OK;
+    p2s_status s0 = tc_prepare(ctx);
+    if (s0 != P2S_OK) return s0;
+    for (int i0 = 0; i0 < n; i0 += kMaxFrames) {
+        const int nb = n - i0 < kMaxFrames ? n - i0 : kMaxFrames;
+        thread_local Params p;
+        std::memset(&p, 0, sizeof p);
+        int tiles = 0;
+        double npx = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            const TcFrame &t = frames[i0 + i];
+            Frame &f = p.fr[i];
+            f.xw = t.xw;
+            f.y = t.y;
+            f.beta16 = (const uint4 *)beta16[i0 + i];
+            f.H = t.H;
+            f.W = t.W;
+            f.tiles_x = (t.W + kStrip - 1) / kStrip;
+            f.tiles_y = (t.H + kBand - 1) / kBand;
+            f.tile_base = tiles;
+            tiles += f.tiles_x * f.tiles_y;
+            npx += (double)t.H * t.W;
+        }
+        p.n_frames = nb;
+        p.tiles_total = tiles;
+        p.stream = (const uint8_t *)ctx->tc.d_H;
+        const Item16 *items = (const Item16 *)ctx->tc_items.data();
+        for (int c = 0; c < kChunks; ++c) {
+            const Item16 &it = items[6 + c];
+            p.item[c] = Item{it.offset, it.bytes, it.n, it.k};
+        }
+        p.ab_fmt = ctx->tc.fmt;
+        p.status = status;
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        const int grid = tiles < sms ? tiles : sms;
+        ProfScope pr(ctx, st, "blur_tc_gather16", 2.0 * ctx->K * ctx->T * npx, npx * (C * 8.0 + kGroups * 16.0));
+        if (C == 3) {
+            P2S_CUDA(cudaFuncSetAttribute(gather_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+            gather_kernel<3><<<grid, kThreads, kSmemBytes, st>>>(p);
+        } else {
+            P2S_CUDA(cudaFuncSetAttribute(gather_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+            gather_kernel<1><<<grid, kThreads, kSmemBytes, st>>>(p);
+        }
+        P2S_CUDA(cudaGetLastError());
+    }
+    return P2S_OK;
+}
+
+}  // namespace p2s

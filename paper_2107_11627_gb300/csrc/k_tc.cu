@@ -458,12 +458,14 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                     ptx::fence_after();
                     if (!got) {
                     } else if (c < kMainChunks) {
-                        uint32_t g0[16], g1[16];
-                        ptx::tmem_ld16(buf + 16 * half, g0);
-                        ptx::tmem_ld16(buf + kMainN + 16 * half, g1);
 #pragma unroll 1
                         for (int u3 = 0; u3 < 3; ++u3) {
                             const int txx = 3 * c + u3;  // tap column 0..32
+                            // G of this tap column; loading the next one ahead would keep two
+                            // copies live across the unroll-1 loop (register moves per tap)
+                            uint32_t g0[16], g1[16];
+                            ptx::tmem_ld16(buf + 32 * u3 + 16 * half, g0);
+                            ptx::tmem_ld16(buf + kMainN + 32 * u3 + 16 * half, g1);
                             float wr[17], wg[17], wb[17];
                             const int base = (2 * rp + 1 + jlo) * kTC + col + 32 - txx;
 #pragma unroll
@@ -481,10 +483,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                             for (int t = 0; t < 16; ++t) {
                                 a[t] = __uint_as_float(g0[t]);
                                 bb[t] = __uint_as_float(g1[t]);
-                            }
-                            if (u3 < 2) {  // next tap column's G while this one computes
-                                ptx::tmem_ld16(buf + 32 * (u3 + 1) + 16 * half, g0);
-                                ptx::tmem_ld16(buf + kMainN + 32 * (u3 + 1) + 16 * half, g1);
                             }
 #pragma unroll
                             for (int t = 0; t < 16; ++t) {

@@ -545,6 +545,11 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
         ctx->field_method = value;
         return P2S_OK;
     }
+    if (option == P2S_OPT_GATHER_SPLIT) {
+        if (value != 0 && value != 1) return einval("gather split is 0 (fused) or 1 (network, then blur)");
+        ctx->gather_split = value;
+        return P2S_OK;
+    }
     return einval("unknown option");
 }
 p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
@@ -575,6 +580,10 @@ p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value) {
     }
     if (option == P2S_OPT_FIELD_METHOD) {
         *value = ctx->field_method;
+        return P2S_OK;
+    }
+    if (option == P2S_OPT_GATHER_SPLIT) {
+        *value = ctx->gather_split;
         return P2S_OK;
     }
     return einval("unknown option");
@@ -751,7 +760,9 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
 static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, const p2s_image *out, int n,
                                      const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s,
                                      Scratch &sc) {
-    std::vector<TcFrame> tf[2];  // C = 1, C = 3
+    std::vector<TcFrame> tf[2];      // C = 1, C = 3
+    std::vector<const void *> b16[2];  // split form: each frame's beta16
+    const bool split = ctx->gather_split != 0;
     struct PostWarp {
         FieldGeom g;
         int C;
@@ -790,8 +801,9 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             fill_batch(&fb, nb, dr, sd);
             const size_t a_bytes = ((size_t)nb * g.Ah * g.Aw * kAlphaStride * sizeof(float) + 255) & ~(size_t)255;
             const size_t f_bytes = (fields_scratch_bytes(g, nb) + 255) & ~(size_t)255;
-            const size_t xw_bytes = (size_t)nb * npx * C * sizeof(float);
-            char *buf = (char *)sc.get(a_bytes + f_bytes + xw_bytes);
+            const size_t xw_bytes = ((size_t)nb * npx * C * sizeof(float) + 255) & ~(size_t)255;
+            const size_t b_bytes = split ? beta16_bytes(H, W, nb) : 0;
+            char *buf = (char *)sc.get(a_bytes + f_bytes + xw_bytes + b_bytes);
             if (!buf) {
                 set_error("device allocation failed for per-call scratch");
                 st = P2S_ENOMEM;
@@ -803,6 +815,8 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             st = launch_fields(ctx, g, fb, alpha, buf + a_bytes, s);
             const bool bw = ctx->blur_then_warp;
             if (st == P2S_OK && !bw) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
+            char *b16buf = buf + a_bytes + f_bytes + xw_bytes;
+            if (st == P2S_OK && split) st = launch_net16(ctx, g, nb, alpha, b16buf, 1, ctx->d_status, s);
             for (int k = 0; k < nb; ++k) {
                 const int f = idx[i0 + k];
                 const float *a_k = alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride;
@@ -810,13 +824,16 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
                 tf[C == 3 ? 1 : 0].push_back(
                     TcFrame{bw ? ip[k] : xwm[k], bw ? xwm[k] : out[f].data, a_k, H, W, g.Ah, g.Aw, 0, 0, 0});
                 if (bw) post_warp.push_back(PostWarp{g, C, xwm[k], a_k, out[f].data});
+                if (split) b16[C == 3 ? 1 : 0].push_back(b16buf + (size_t)k * beta16_bytes(H, W, 1));
             }
         }
     }
-    if (st == P2S_OK && !tf[1].empty())
-        st = launch_tc(ctx, kTcFull, tf[1].data(), (int)tf[1].size(), 3, nullptr, nullptr, ctx->d_status, s);
-    if (st == P2S_OK && !tf[0].empty())
-        st = launch_tc(ctx, kTcFull, tf[0].data(), (int)tf[0].size(), 1, nullptr, nullptr, ctx->d_status, s);
+    for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
+        if (tf[ci].empty()) continue;
+        const int C = ci ? 3 : 1;
+        st = split ? launch_gather_split(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
+                   : launch_tc(ctx, kTcFull, tf[ci].data(), (int)tf[ci].size(), C, nullptr, nullptr, ctx->d_status, s);
+    }
     for (const PostWarp &w : post_warp) {
         if (st != P2S_OK) break;
         const float *in1[1] = {w.in};
@@ -989,8 +1006,8 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     int option = 0;
     std::vector<int> cand;
     if (tc && ctx->form == P2S_GATHER) {
-        option = P2S_OPT_GATHER_BAND_ROWS;
-        cand = {32, 16};
+        option = P2S_OPT_GATHER_SPLIT;
+        cand = {0, 1};
     } else if (tc && ctx->form == P2S_SCATTER) {
         option = P2S_OPT_SCATTER_SEGMENT_ROWS;
         cand = {32, 64, 128, 256, 1024};

@@ -116,6 +116,7 @@ struct p2s_ctx {
     int use_graphs = 0;
     int blur_then_warp = 0;  // P2S_OPT_BLUR_THEN_WARP
     int field_method = 0;    // P2S_OPT_FIELD_METHOD: 0 Fourier filtering, 1 dense draw
+    int gather_split = 0;    // P2S_OPT_GATHER_SPLIT
     std::map<int, void *> dense_L;  // dense draw: FP32 Cholesky factors [n_kernels][n][n] by n
     void *arena = nullptr;
     size_t arena_bytes = 0;
@@ -175,6 +176,10 @@ struct TcFrame {
     int H, W, Ah, Aw, tiles_x, tiles_y, tile_base;
 };
 constexpr int kMaxTcFrames = 256;  // frames per persistent launch (the table is a kernel parameter)
+// Blur-only tensor-core gather over frames whose beta the network kernel
+// wrote (launch_net16 with the bias-fold ones); beta16[i] is frame i's.
+p2s_status launch_gather_split(p2s_ctx *ctx, const TcFrame *frames, const void *const *beta16, int n, int C,
+                               int *status, cudaStream_t st);
 p2s_status launch_tc(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
                      float *beta_out, int *status, cudaStream_t st);
 constexpr int kTcFull = 0, kTcMlpOnly = 1, kTcBlurOnly = 2;

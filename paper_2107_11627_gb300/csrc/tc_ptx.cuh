@@ -127,6 +127,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test (try_wait may suspend the thread for a while when the
+// phase is not complete; a thread polling several barriers must not).
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // ---- bulk copy (TMA, non-tensor) -------------------------------------------
 
 // global -> shared, completion counted on `bar` in bytes; addresses and size

@@ -318,7 +318,8 @@ class Simulator:
         _check(lib().p2s_selftest_stall(self.ctx, _stream_handle(stream)), "p2s_selftest_stall")
 
     OPTIONS = {"scatter_segment_rows": 1, "graphs": 2, "graph_instantiations": 3, "graph_updates": 4,
-               "gather_band_rows": 5, "blur_then_warp": 6, "field_method": 7}
+               "gather_band_rows": 5, "blur_then_warp": 6, "field_method": 7,
+               "gather_split": 8}
 
     def set_option(self, name: str, value: int):
         _check(lib().p2s_set_option(self.ctx, self.OPTIONS[name], int(value)), "p2s_set_option")

@@ -20,6 +20,11 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
+# fused vs split gather: same rounding points, different FP32 summation order; an
+# order change can move a beta entry to the neighbouring 16-bit value
+SPLIT_VS_FUSED = 5e-5
+
+
 def _sim(prec="fp16", form="gather", graphs=False):
     from paper_2107_11627_gb300 import p2s
 
@@ -120,13 +125,17 @@ def test_autotune_picks_a_candidate_and_keeps_results(form):
     xs = [torch.from_numpy(x).cuda() for x in _frames(shapes)]
     before = sim.simulate(xs, [2.0, 4.0], [3, 4])
     r = sim.autotune(xs, [2.0, 4.0], [3, 4], reps=1)
-    assert r["option"] == ("gather_band_rows" if form == "gather" else "scatter_segment_rows")
+    assert r["option"] == ("gather_split" if form == "gather" else "scatter_segment_rows")
     assert len(r["candidates"]) >= 2 and r["best"] in r["candidates"]
     assert sim.get_option(r["option"]) == r["best"]
     after = sim.simulate(xs, [2.0, 4.0], [3, 4])
     sim.check()
+    # fused and split gather kernels share every rounding point but not the order of
+    # the FP32 sums, so a few beta entries round to the neighbouring FP16 value
+    # (2^-11 relative); each side stays within 2.5e-4 of the FP64 oracle
+    tol = SPLIT_VS_FUSED if form == "gather" else 1e-6
     for u, v in zip(before, after):
-        assert rel(v.cpu().numpy(), u.cpu().numpy()) < 1e-6
+        assert rel(v.cpu().numpy(), u.cpu().numpy()) < tol
 
 
 @pytest.mark.parametrize("prec,form", [("fp16", "gather"), ("fp16", "scatter"), ("fp32", "scatter")])
@@ -146,3 +155,52 @@ def test_blur_then_warp_order(prec, form):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form=form, order="blur_warp")
         assert rel(ys[i].cpu().numpy(), ref.y) < tol, (i, rel(ys[i].cpu().numpy(), ref.y))
+
+
+@pytest.mark.parametrize("c", [3, 1])
+def test_split_gather_matches_oracle_and_fused(c):
+    """Network kernel, then the blur-only tensor-core gather (three accumulating warps per
+    lane quadrant): same rounding points as the fused kernel, so within FP32 summation
+    order of it, and within the 16-bit bound of the oracle.  Sizes span several tiles,
+    a ragged column tail and an odd last row pair."""
+    shapes = [(97, 300), (33, 129), (1, 1), (64, 128)]
+    xs = _frames(shapes, c=c, first=2400)
+    dr, seeds = [1.5, 3.0, 2.0, 5.0], [71, 72, 73, 74]
+    fused = _sim()
+    split = _sim()
+    split.set_option("gather_split", 1)
+    assert split.get_option("gather_split") == 1
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    ya = fused.simulate(xd, dr, seeds)
+    yb = split.simulate(xd, dr, seeds)
+    fused.check()
+    split.check()
+    for i in range(len(xs)):
+        assert rel(yb[i].cpu().numpy(), ya[i].cpu().numpy()) < SPLIT_VS_FUSED, (i, shapes[i])
+    for i in (0, 1):
+        ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
+                                    CorrParams(8, (16.0,)), (33, 33), form="gather")
+        assert rel(yb[i].cpu().numpy(), ref.y) < TOL_BF16, (i, rel(yb[i].cpu().numpy(), ref.y))
+    (alone,) = split.simulate([xd[1]], [dr[1]], [seeds[1]])
+    split.check()
+    assert torch.equal(alone, yb[1])
+
+
+def test_split_gather_blur_then_warp_and_graphs():
+    shapes = [(96, 160), (70, 130)]
+    xs = [torch.from_numpy(x).cuda() for x in _frames(shapes, first=2500)]
+    a = _sim()
+    b = _sim(graphs=True)
+    for s in (a, b):
+        s.set_option("gather_split", 1)
+        s.set_option("blur_then_warp", 1)
+    ya = a.simulate(xs, [2.0, 4.0], [5, 6])
+    yb = b.simulate(xs, [2.0, 4.0], [5, 6])
+    a.check()
+    b.check()
+    for i in range(2):
+        assert torch.equal(ya[i], yb[i])
+        ref = oracle.frame.simulate(xs[i].cpu().numpy().astype(np.float64), [5, 6][i], [2.0, 4.0][i], cfg2()["H"],
+                                    cfg2()["layers"], CorrParams(8, (16.0,)), (33, 33), form="gather",
+                                    order="blur_warp")
+        assert rel(ya[i].cpu().numpy(), ref.y) < TOL_BF16
