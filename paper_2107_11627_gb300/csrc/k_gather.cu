@@ -96,13 +96,10 @@ __device__ __forceinline__ int frame_of(const Params &p, int tile) {
     return lo;
 }
 
-// tap rows of group g in a main chunk: [11 g, 11 g + n), n = 11, 11, 10
-__host__ __device__ constexpr int grp_r0(int g) { return 11 * g; }
-__host__ __device__ constexpr int grp_n(int g) { return g == 2 ? 10 : 11; }
-// first TMEM column of a group's 16-column load inside a 32-column tap column
-// (kept inside the block so the second buffer's last load ends at column 512)
-__host__ __device__ constexpr int grp_ls(int g) { return g == 2 ? 16 : 11 * g; }
-static_assert(grp_ls(2) + 16 <= 32 && grp_r0(2) - grp_ls(2) + grp_n(2) <= 16, "group 2 load window");
+// Tap rows of group g in a main chunk: [11 g, 11 g + 11); group 2 has only
+// 10 (rows 22..31), its 11th weight is forced to 0.  One code path serves all
+// three groups (distinct unrolled bodies per group thrash the instruction cache).
+constexpr int kNT = 11;
 
 // One staged pixel of x: (R, G) and (B, 0) as FP16 pairs, 8 bytes.
 __device__ __forceinline__ uint2 encode_px(float r, float g, float b) {
@@ -118,14 +115,17 @@ __device__ __forceinline__ void decode_px(uint2 v, float &r, float &g, float &b)
     b = (C == 3) ? __low2float(*reinterpret_cast<const __half2 *>(&v.y)) : 0.f;
 }
 
-template <int C, int G>
+template <int C>
 __device__ __forceinline__ void accumulate_pair(const Params &p, const uint2 *x16, uint32_t lane_base, int col, int rp,
-                                                uint32_t bar0, uint32_t &uses, bool &ok, const Ctl &ctl, int lane,
-                                                float (&acc)[2][3]) {
-    constexpr int R0 = grp_r0(G), NT = grp_n(G), NW = NT + 1, LS = grp_ls(G), OFF = R0 - LS;
+                                                int grp, uint32_t bar0, uint32_t &uses, bool &ok, const Ctl &ctl,
+                                                int lane, float (&acc)[2][3]) {
+    constexpr int NT = kNT, NW = NT + 1;
     auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
-    const int wbase = 2 * rp + 33 - R0 - NT;  // first window row of this group
-    const uint2 *xw0 = x16 + wbase * kTC + col + 32;  // window of tap column txx starts at xw0 - txx
+    const int R0 = 11 * grp;
+    const uint32_t last = grp == 2 ? 9u : 10u;  // column of the 11th load (group 2: a valid, unused one)
+    const float keep_last = grp == 2 ? 0.f : 1.f;
+    // window rows of tap row R0 + t: NT - 1 - t (output row 0) and NT - t (row 1)
+    const uint2 *xw0 = x16 + (2 * rp + 33 - R0 - NT) * kTC + col + 32;  // tap column txx: xw0 - txx
     for (int c = 0; c < kChunks; ++c) {
         const int b = c & 1;
         const uint32_t buf = lane_base + colDB(b);
@@ -139,9 +139,10 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint2 *x1
             for (int u3 = 0; u3 < 3; ++u3) {
                 // G of this tap column (loading the next one ahead would keep two copies
                 // live across the loop: register moves for every tap)
-                uint32_t g0[16], g1[16];
-                ptx::tmem_ld16(buf + 32 * u3 + LS, g0);
-                ptx::tmem_ld16(buf + kMainN + 32 * u3 + LS, g1);
+                const uint32_t c0 = buf + 32 * u3 + R0, c1 = c0 + kMainN;
+                uint32_t g0[11], g1[11];
+                ptx::tmem_ld11(c0, c0 + 8, c0 + last, g0);
+                ptx::tmem_ld11(c1, c1 + 8, c1 + last, g1);
                 const int txx = 3 * c + u3;
                 float wr[NW], wg[NW], wb[NW];
 #pragma unroll
@@ -151,12 +152,13 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint2 *x1
                 float a[NT], bb[NT];
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    a[t] = __uint_as_float(g0[OFF + t]);
-                    bb[t] = __uint_as_float(g1[OFF + t]);
+                    a[t] = __uint_as_float(g0[t]);
+                    bb[t] = __uint_as_float(g1[t]);
                 }
+                a[NT - 1] *= keep_last;
+                bb[NT - 1] *= keep_last;
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    // tap row R0 + t: window rows NT - 1 - t (row 0) and NT - t (row 1)
                     acc[0][0] = fmaf(a[t], wr[NT - 1 - t], acc[0][0]);
                     acc[1][0] = fmaf(bb[t], wr[NT - t], acc[1][0]);
                     if (C == 3) {
@@ -168,20 +170,20 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint2 *x1
                 }
             }
         } else {
-            // last tap row (tap row 32): tap columns [11 G, 11 G + 11), window rows 2 rp + i
-            uint32_t g0[16], g1[16];
-            ptx::tmem_ld16(buf + 11 * G, g0);
-            ptx::tmem_ld16(buf + kMainN + 11 * G, g1);
+            // last tap row (tap row 32): tap columns [11 grp, 11 grp + 11), window rows 2 rp + i
+            const uint32_t c0 = buf + R0, c1 = c0 + kMainN;
+            uint32_t g0[11], g1[11];
+            ptx::tmem_ld11(c0, c0 + 8, c0 + 10, g0);
+            ptx::tmem_ld11(c1, c1 + 8, c1 + 10, g1);
             ptx::tmem_wait_ld_dep(g0);
             ptx::tmem_wait_ld_dep(g1);
+            const uint2 *xr = x16 + (2 * rp) * kTC + col + 32 - R0;
 #pragma unroll
             for (int q = 0; q < 11; ++q) {
-                const int txx = 11 * G + q;
-                const int i0 = (2 * rp) * kTC + col + 32 - txx, i1 = i0 + kTC;
                 const float a = __uint_as_float(g0[q]), b2 = __uint_as_float(g1[q]);
                 float r0, gg0, b0, r1, gg1, b1;
-                decode_px<C>(x16[i0], r0, gg0, b0);
-                decode_px<C>(x16[i1], r1, gg1, b1);
+                decode_px<C>(xr[-q], r0, gg0, b0);
+                decode_px<C>(xr[kTC - q], r1, gg1, b1);
                 acc[0][0] = fmaf(a, r0, acc[0][0]);
                 acc[1][0] = fmaf(b2, r1, acc[1][0]);
                 if (C == 3) {
@@ -372,12 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) acc[i][ch] = 0.f;
-                if (grp == 0)
-                    accumulate_pair<C, 0>(p, x16, lane_base, col, rp, bar0, uses, ok, ctl, lane, acc);
-                else if (grp == 1)
-                    accumulate_pair<C, 1>(p, x16, lane_base, col, rp, bar0, uses, ok, ctl, lane, acc);
-                else
-                    accumulate_pair<C, 2>(p, x16, lane_base, col, rp, bar0, uses, ok, ctl, lane, acc);
+                accumulate_pair<C>(p, x16, lane_base, col, rp, grp, bar0, uses, ok, ctl, lane, acc);
                 // ---- add the three groups' partial sums, write the row pair ----
                 if (grp > 0) {
                     float *xc = xchg + (grp - 1) * kStrip * 6;
