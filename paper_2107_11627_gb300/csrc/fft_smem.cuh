@@ -37,5 +37,45 @@ __device__ __forceinline__ float2 *fft_rows(float2 *a, float2 *b, const float2 *
     return a;
 }
 
+// The same transform with N = 2^LOGN known at compile time: index arithmetic
+// by shifts and masks, stages unrolled.  Same butterflies in the same order.
+template <int LOGN>
+__device__ __forceinline__ float2 *fft_rows_t(float2 *a, float2 *b, const float2 *tw, int R, bool inverse) {
+    constexpr int N = 1 << LOGN, HALF = N >> 1;
+#pragma unroll
+    for (int s = 0; s < LOGN; ++s) {
+        const int ns = 1 << s;
+        const int tshift = LOGN - 1 - s;  // twiddle stride N / (2 ns)
+        for (int idx = threadIdx.x; idx < R * HALF; idx += blockDim.x) {
+            const int r = idx >> (LOGN - 1), j = idx & (HALF - 1);
+            const int k = j & (ns - 1);
+            const float2 v0 = a[r * N + j];
+            float2 w = tw[k << tshift];
+            if (inverse) w.y = -w.y;
+            const float2 v1 = cmul(a[r * N + j + HALF], w);
+            const int d = ((j - k) << 1) + k;
+            b[r * N + d] = make_float2(v0.x + v1.x, v0.y + v1.y);
+            b[r * N + d + ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+        }
+        __syncthreads();
+        float2 *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// fft_rows with a compile-time length for the common sizes.
+__device__ __forceinline__ float2 *fft_rows_any(float2 *a, float2 *b, const float2 *tw, int N, int R, bool inverse) {
+    switch (N) {
+        case 32: return fft_rows_t<5>(a, b, tw, R, inverse);
+        case 64: return fft_rows_t<6>(a, b, tw, R, inverse);
+        case 128: return fft_rows_t<7>(a, b, tw, R, inverse);
+        case 256: return fft_rows_t<8>(a, b, tw, R, inverse);
+        case 512: return fft_rows_t<9>(a, b, tw, R, inverse);
+        default: return fft_rows(a, b, tw, N, R, inverse);
+    }
+}
+
 }  // namespace fftsm
 }  // namespace p2s

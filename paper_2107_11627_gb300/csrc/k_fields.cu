@@ -21,7 +21,7 @@ namespace p2s {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kFftElems = 4096;  // complex elements per ping-pong buffer
+constexpr int kFftElems = 2048;  // complex elements per ping-pong buffer (32 KB per CTA: several CTAs per SM)
 
 struct U4 {
     uint32_t x, y, z, w;
@@ -85,7 +85,7 @@ __global__ void noise_kernel(unsigned long long seed, int mode, long long n, flo
 }
 
 using fftsm::cmul;
-using fftsm::fft_rows;
+using fftsm::fft_rows_any;
 
 // Row pass: white noise rows (y0, y0+1) packed as one complex row, filtered
 // along x; columns [0, Aw) of both rows go to t[frame][mode][y][x].
@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(kThreads) row_filter_kernel(FrameBatch fb, int
     const int y_base = blockIdx.x * R * 2;  // first torus row of this CTA
     const int n_rows = min(2 * R, Fh - y_base);
     const unsigned long long seed = fb.seed[frame];
+    const int lgF = __ffs(Fw) - 1;
     // noise: samples [y_base*Fw, (y_base+n_rows)*Fw) of stream (seed, mode), quad by quad
     const int q0 = (y_base * Fw) >> 2, q1 = ((y_base + n_rows) * Fw + 3) >> 2;
     for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) row_filter_kernel(FrameBatch fb, int
         for (int i = 0; i < 4; ++i) {
             const int s = 4 * q + i - y_base * Fw;
             if (s < 0 || s >= n_rows * Fw) continue;
-            const int row = s / Fw, x = s - row * Fw;
+            const int row = s >> lgF, x = s & (Fw - 1);  // Fw is a power of two
             float *dst = (float *)&buf0[(row >> 1) * Fw + x];
             dst[row & 1] = z[i];
         }
@@ -122,15 +123,15 @@ __global__ void __launch_bounds__(kThreads) row_filter_kernel(FrameBatch fb, int
         for (int x = threadIdx.x; x < Fw; x += blockDim.x) buf0[(n_rows >> 1) * Fw + x].y = 0.0f;
     __syncthreads();
     const int Rk = (n_rows + 1) >> 1;
-    float2 *res = fft_rows(buf0, buf1, stw, Fw, Rk, false);
+    float2 *res = fft_rows_any(buf0, buf1, stw, Fw, Rk, false);
     for (int i = threadIdx.x; i < Rk * Fw; i += blockDim.x) {
-        const float gg = sg[i % Fw];
+        const float gg = sg[i & (Fw - 1)];
         res[i].x *= gg;
         res[i].y *= gg;
     }
     __syncthreads();
     float2 *other = res == buf0 ? buf1 : buf0;
-    res = fft_rows(res, other, stw, Fw, Rk, true);
+    res = fft_rows_any(res, other, stw, Fw, Rk, true);
     float *tf = t + ((size_t)frame * kModes + mode) * Fh * Aw;
     for (int i = threadIdx.x; i < n_rows * Aw; i += blockDim.x) {
         const int row = i / Aw, x = i - row * Aw;
@@ -158,23 +159,24 @@ __global__ void __launch_bounds__(kThreads) col_filter_kernel(int Fh, int Ah, in
     const int n_cols = min(2 * R, Aw - x_base);
     const int Rk = (n_cols + 1) >> 1;
     const float *tf = t + ((size_t)frame * kModes + mode) * Fh * Aw;
+    const int lgF = __ffs(Fh) - 1;
     for (int i = threadIdx.x; i < Rk * Fh; i += blockDim.x) {
-        const int c = i / Fh, y = i - c * Fh;
+        const int c = i >> lgF, y = i & (Fh - 1);
         const int x = x_base + 2 * c;
         const float re = tf[(size_t)y * Aw + x];
         const float im = (2 * c + 1 < n_cols) ? tf[(size_t)y * Aw + x + 1] : 0.0f;
         buf0[c * Fh + y] = make_float2(re, im);
     }
     __syncthreads();
-    float2 *res = fft_rows(buf0, buf1, stw, Fh, Rk, false);
+    float2 *res = fft_rows_any(buf0, buf1, stw, Fh, Rk, false);
     for (int i = threadIdx.x; i < Rk * Fh; i += blockDim.x) {
-        const float gg = sg[i % Fh];
+        const float gg = sg[i & (Fh - 1)];  // Fh is a power of two
         res[i].x *= gg;
         res[i].y *= gg;
     }
     __syncthreads();
     float2 *other = res == buf0 ? buf1 : buf0;
-    res = fft_rows(res, other, stw, Fh, Rk, true);
+    res = fft_rows_any(res, other, stw, Fh, Rk, true);
     float *ff = f + ((size_t)frame * kModes + mode) * Ah * Aw;
     for (int i = threadIdx.x; i < n_cols * Ah; i += blockDim.x) {
         const int cc = i / Ah, y = i - cc * Ah;
