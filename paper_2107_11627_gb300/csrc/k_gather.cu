@@ -2,10 +2,11 @@
 // network kernel's 16-bit operand layout: the split alternative to the fused
 // kernel, chosen by P2S_OPT_GATHER_SPLIT.
 //
-// With the network out of the kernel, the tap accumulation gets three warps
-// per TMEM lane quadrant (12 accumulating warps) instead of two: each takes a
-// third of the tap rows of every chunk, with its own window of x.  Per row
-// pair of a 128 x 32 tile:
+// With the network out of the kernel, the tap accumulation gets four warps
+// per TMEM lane quadrant (16 accumulating warps) instead of two: each takes a
+// quarter of the tap rows of every chunk (8), with its own window of x.  x is
+// staged as vertical pixel pairs, so a window of 9 rows costs five 16-byte
+// loads per tap column.  Per row pair of a 128 x 32 tile:
 //   producer  beta rows (2 x 14 runs of 16-byte groups) into a staging buffer
 //             with 1-D bulk copies, basis chunks into a 2-slot ring;
 //   warps of groups 0, 1 move their row's beta from the staging buffer into
@@ -13,7 +14,7 @@
 //   MMA       G = beta H chunk by chunk (N = 96: 3 tap columns x 32 tap rows,
 //             then N = 48 for the last tap row), two TMEM buffers;
 //   gather    y_c[q] += G[q, t] x_c[q - o(t)], x staged as FP16 RGB, FP32
-//             accumulation; the three groups' partial sums are added through
+//             accumulation; the four groups' partial sums are added through
 //             shared memory and written.
 // Every wait is bounded.
 #include <cuda_bf16.h>
@@ -44,20 +45,21 @@ constexpr int kChunks = kMainChunks + 1;
 constexpr int kSlot = 32768;
 constexpr int kSlots = 2;
 constexpr int kGroups = 14;                       // beta16 k-groups
-constexpr int kGroupsEpi = 3;                     // accumulating groups of 4 warps
-constexpr int kEpi = 128 * kGroupsEpi;            // 384
-constexpr int kThreads = 64 + kEpi;               // 448
+constexpr int kGroupsEpi = 4;                     // accumulating groups of 4 warps
+constexpr int kEpi = 128 * kGroupsEpi;            // 512
+constexpr int kThreads = 64 + kEpi;               // 576
+constexpr int kXPairs = kTR / 2 + 1;              // x tile rows (2 j - 1, 2 j), j = 0 .. 32
 constexpr int kBetaRow = kGroups * kStrip * 16;   // 28,672 B per staged row
 
 __host__ __device__ constexpr uint32_t colBeta(int r) { return r ? 56u : 0u; }
 __host__ __device__ constexpr uint32_t colDB(int h) { return h ? 320u : 128u; }
 
 constexpr int kOffRing = 0;
-constexpr int kOffX = kOffRing + kSlots * kSlot;           // uint2 [kTR][kTC]
-constexpr int kOffBeta = kOffX + kTR * kTC * 8;            // [2 rows][14][128][16 B]
-constexpr int kOffXchg = kOffBeta + 2 * kBetaRow;          // float [2][128][6]
+constexpr int kOffX = kOffRing + kSlots * kSlot;           // uint4 [kXPairs][kTC]: two FP16 RGB pixels
+constexpr int kOffBeta = kOffX + kXPairs * kTC * 16;       // [2 rows][14][128][16 B]
+constexpr int kOffXchg = kOffBeta + 2 * kBetaRow;          // float [3][128][6]
 enum Bar { kFull0 = 0, kEmpty0 = 2, kBStaged = 4, kBFree = 5, kBReady = 6, kDFull0 = 7, kDEmpty0 = 9, kNBar = 11 };
-constexpr int kOffBar = kOffXchg + 2 * kStrip * 6 * 4;
+constexpr int kOffBar = kOffXchg + (kGroupsEpi - 1) * kStrip * 6 * 4;
 constexpr int kOffMisc = kOffBar + kNBar * 8;
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
@@ -96,36 +98,35 @@ __device__ __forceinline__ int frame_of(const Params &p, int tile) {
     return lo;
 }
 
-// Tap rows of group g in a main chunk: [11 g, 11 g + 11); group 2 has only
-// 10 (rows 22..31), its 11th weight is forced to 0.  One code path serves all
-// three groups (distinct unrolled bodies per group thrash the instruction cache).
-constexpr int kNT = 11;
+// Tap rows of group g in a main chunk: [8 g, 8 g + 8); in the last chunk
+// (tap row 32) tap columns [9 g, 9 g + 9) below 33.  One code path serves all
+// groups (distinct unrolled bodies per group thrash the instruction cache).
+constexpr int kNT = 8;
 
-// One staged pixel of x: (R, G) and (B, 0) as FP16 pairs, 8 bytes.
+// x pixel as FP16: (R, G) and (B, 0)
 __device__ __forceinline__ uint2 encode_px(float r, float g, float b) {
     const __half2 rg = __floats2half2_rn(r, g), b0 = __floats2half2_rn(b, 0.f);
     return make_uint2(*reinterpret_cast<const uint32_t *>(&rg), *reinterpret_cast<const uint32_t *>(&b0));
 }
 
 template <int C>
-__device__ __forceinline__ void decode_px(uint2 v, float &r, float &g, float &b) {
-    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+__device__ __forceinline__ void decode_px(uint32_t rg_w, uint32_t b_w, float &r, float &g, float &b) {
+    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&rg_w));
     r = rg.x;
     g = (C == 3) ? rg.y : 0.f;
-    b = (C == 3) ? __low2float(*reinterpret_cast<const __half2 *>(&v.y)) : 0.f;
+    b = (C == 3) ? __low2float(*reinterpret_cast<const __half2 *>(&b_w)) : 0.f;
 }
 
 template <int C>
-__device__ __forceinline__ void accumulate_pair(const Params &p, const uint2 *x16, uint32_t lane_base, int col, int rp,
+__device__ __forceinline__ void accumulate_pair(const Params &p, const uint4 *xp, uint32_t lane_base, int col, int rp,
                                                 int grp, uint32_t bar0, uint32_t &uses, bool &ok, const Ctl &ctl,
                                                 int lane, float (&acc)[2][3]) {
     constexpr int NT = kNT, NW = NT + 1;
     auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
-    const int R0 = 11 * grp;
-    const uint32_t last = grp == 2 ? 9u : 10u;  // column of the 11th load (group 2: a valid, unused one)
-    const float keep_last = grp == 2 ? 0.f : 1.f;
-    // window rows of tap row R0 + t: NT - 1 - t (output row 0) and NT - t (row 1)
-    const uint2 *xw0 = x16 + (2 * rp + 33 - R0 - NT) * kTC + col + 32;  // tap column txx: xw0 - txx
+    const int R0 = NT * grp;
+    // Window rows r_s .. r_s + 8 with r_s = 2 rp + 25 - R0 (odd) = pixel pairs j_s .. j_s + 4,
+    // j_s = (r_s + 1) / 2; tap row R0 + t reads window row 7 - t (output row 0) and 8 - t (row 1).
+    const int xw0 = (rp + 13 - 4 * grp) * kTC + col + 32;  // tap column txx: xw0 - txx
     for (int c = 0; c < kChunks; ++c) {
         const int b = c & 1;
         const uint32_t buf = lane_base + colDB(b);
@@ -137,60 +138,60 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint2 *x1
         } else if (c < kMainChunks) {
 #pragma unroll 1
             for (int u3 = 0; u3 < 3; ++u3) {
-                // G of this tap column (loading the next one ahead would keep two copies
-                // live across the loop: register moves for every tap)
-                const uint32_t c0 = buf + 32 * u3 + R0, c1 = c0 + kMainN;
-                uint32_t g0[11], g1[11];
-                ptx::tmem_ld11(c0, c0 + 8, c0 + last, g0);
-                ptx::tmem_ld11(c1, c1 + 8, c1 + last, g1);
+                const uint32_t c0 = buf + 32 * u3 + R0;
+                uint32_t g0[8], g1[8];
+                ptx::tmem_ld8(c0, g0);
+                ptx::tmem_ld8(c0 + kMainN, g1);
                 const int txx = 3 * c + u3;
-                float wr[NW], wg[NW], wb[NW];
+                float wr[NW + 1], wg[NW + 1], wb[NW + 1];
 #pragma unroll
-                for (int m = 0; m < NW; ++m) decode_px<C>(xw0[m * kTC - txx], wr[m], wg[m], wb[m]);
+                for (int k = 0; k < (NW + 1) / 2; ++k) {
+                    const uint4 v = xp[xw0 + k * kTC - txx];
+                    decode_px<C>(v.x, v.y, wr[2 * k], wg[2 * k], wb[2 * k]);
+                    decode_px<C>(v.z, v.w, wr[2 * k + 1], wg[2 * k + 1], wb[2 * k + 1]);
+                }
                 ptx::tmem_wait_ld_dep(g0);
                 ptx::tmem_wait_ld_dep(g1);
-                float a[NT], bb[NT];
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    a[t] = __uint_as_float(g0[t]);
-                    bb[t] = __uint_as_float(g1[t]);
-                }
-                a[NT - 1] *= keep_last;
-                bb[NT - 1] *= keep_last;
-#pragma unroll
-                for (int t = 0; t < NT; ++t) {
-                    acc[0][0] = fmaf(a[t], wr[NT - 1 - t], acc[0][0]);
-                    acc[1][0] = fmaf(bb[t], wr[NT - t], acc[1][0]);
+                    const float a = __uint_as_float(g0[t]), bb = __uint_as_float(g1[t]);
+                    acc[0][0] = fmaf(a, wr[NT - 1 - t], acc[0][0]);
+                    acc[1][0] = fmaf(bb, wr[NT - t], acc[1][0]);
                     if (C == 3) {
-                        acc[0][1] = fmaf(a[t], wg[NT - 1 - t], acc[0][1]);
-                        acc[0][2] = fmaf(a[t], wb[NT - 1 - t], acc[0][2]);
-                        acc[1][1] = fmaf(bb[t], wg[NT - t], acc[1][1]);
-                        acc[1][2] = fmaf(bb[t], wb[NT - t], acc[1][2]);
+                        acc[0][1] = fmaf(a, wg[NT - 1 - t], acc[0][1]);
+                        acc[0][2] = fmaf(a, wb[NT - 1 - t], acc[0][2]);
+                        acc[1][1] = fmaf(bb, wg[NT - t], acc[1][1]);
+                        acc[1][2] = fmaf(bb, wb[NT - t], acc[1][2]);
                     }
                 }
             }
         } else {
-            // last tap row (tap row 32): tap columns [11 grp, 11 grp + 11), window rows 2 rp + i
-            const uint32_t c0 = buf + R0, c1 = c0 + kMainN;
-            uint32_t g0[11], g1[11];
-            ptx::tmem_ld11(c0, c0 + 8, c0 + 10, g0);
-            ptx::tmem_ld11(c1, c1 + 8, c1 + 10, g1);
+            // last tap row (tap row 32): tap columns [9 grp, 9 grp + 9) below 33; output row 0
+            // reads tile row 2 rp (second pixel of pair rp), row 1 tile row 2 rp + 1 (first of rp + 1)
+            uint32_t g0[9], g1[9];
+            ptx::tmem_ld9(buf + 9 * grp, g0);
+            ptx::tmem_ld9(buf + kMainN + 9 * grp, g1);
             ptx::tmem_wait_ld_dep(g0);
             ptx::tmem_wait_ld_dep(g1);
-            const uint2 *xr = x16 + (2 * rp) * kTC + col + 32 - R0;
+            const uint2 *xh = reinterpret_cast<const uint2 *>(xp);
+            const int xr0 = 2 * (rp * kTC + col + 32 - 9 * grp) + 1, xr1 = xr0 + 2 * kTC - 1;
+            const int nq = min(9, 33 - 9 * grp);
 #pragma unroll
-            for (int q = 0; q < 11; ++q) {
-                const float a = __uint_as_float(g0[q]), b2 = __uint_as_float(g1[q]);
-                float r0, gg0, b0, r1, gg1, b1;
-                decode_px<C>(xr[-q], r0, gg0, b0);
-                decode_px<C>(xr[kTC - q], r1, gg1, b1);
-                acc[0][0] = fmaf(a, r0, acc[0][0]);
-                acc[1][0] = fmaf(b2, r1, acc[1][0]);
-                if (C == 3) {
-                    acc[0][1] = fmaf(a, gg0, acc[0][1]);
-                    acc[0][2] = fmaf(a, b0, acc[0][2]);
-                    acc[1][1] = fmaf(b2, gg1, acc[1][1]);
-                    acc[1][2] = fmaf(b2, b1, acc[1][2]);
+            for (int q = 0; q < 9; ++q) {
+                if (q < nq) {
+                    const float a = __uint_as_float(g0[q]), b2 = __uint_as_float(g1[q]);
+                    const uint2 v0 = xh[xr0 - 2 * q], v1 = xh[xr1 - 2 * q];
+                    float r0, gg0, b0, r1, gg1, b1;
+                    decode_px<C>(v0.x, v0.y, r0, gg0, b0);
+                    decode_px<C>(v1.x, v1.y, r1, gg1, b1);
+                    acc[0][0] = fmaf(a, r0, acc[0][0]);
+                    acc[1][0] = fmaf(b2, r1, acc[1][0]);
+                    if (C == 3) {
+                        acc[0][1] = fmaf(a, gg0, acc[0][1]);
+                        acc[0][2] = fmaf(a, b0, acc[0][2]);
+                        acc[1][1] = fmaf(b2, gg1, acc[1][1]);
+                        acc[1][2] = fmaf(b2, b1, acc[1][2]);
+                    }
                 }
             }
         }
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = ptx::smem_u32(sm);
-    uint2 *x16 = (uint2 *)(sm + kOffX);
+    uint4 *xp = (uint4 *)(sm + kOffX);
     const uint4 *sbeta = (const uint4 *)(sm + kOffBeta);
     float *xchg = (float *)(sm + kOffXchg);
     const uint32_t bar0 = sbase + kOffBar;
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
             }
         }
     } else {
-        // ---------------- 12 accumulating warps: three per TMEM lane quadrant ----------------
+        // ---------------- 16 accumulating warps: four per TMEM lane quadrant ----------------
         const int e = warp - 2;
         const int grp = e >> 2;
         const int quad = warp & 3;
@@ -325,6 +326,28 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
         const int tid_e = threadIdx.x - 64;
         uint32_t pairs = 0, uses = 0;
         bool ok = true;
+        // beta of row 2 rp + grp of pair number k (this CTA's count) into TMEM: groups 0 and 1;
+        // the MMAs of the pair wait for it, the producer then stages the next pair's
+        auto copy_beta = [&](uint32_t k) {
+            if (grp >= 2) return;
+            ok = __all_sync(0xffffffffu, wait_bar(BAR(kBStaged), k & 1, ctl, 32) && ok);
+            if (ok) {
+                const uint4 *src = sbeta + grp * (kBetaRow / 16) + col;
+#pragma unroll
+                for (int q = 0; q < kGroups / 2; ++q) {
+                    const uint4 v0 = src[(2 * q) * kStrip], v1 = src[(2 * q + 1) * kStrip];
+                    const uint32_t u[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                    ptx::tmem_st8(lane_base + colBeta(grp) + 8 * q, u);
+                }
+                ptx::tmem_wait_st();
+            }
+            ptx::fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                ptx::mbar_arrive(BAR(kBFree));
+                ptx::mbar_arrive(BAR(kBReady));
+            }
+        };
         for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
             const int f = frame_of(p, tile);
             const Frame &F = p.fr[f];
@@ -333,49 +356,37 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
             const int r_band = tyy * kBand, c0 = txx * kStrip;
             const int npair = n_pairs_of(tile);
             ptx::named_bar(1, kEpi);  // previous tile fully consumed
-            for (int i = tid_e; i < kTR * kTC; i += kEpi) {
-                const int tr = i / kTC, tcol = i - tr * kTC;
-                const int gr = r_band - kHalo + tr, gc = c0 - kHalo + tcol;
-                float r = 0.f, g = 0.f, b = 0.f;
-                if (gr >= 0 && gr < F.H && gc >= 0 && gc < F.W) {
-                    const float *px = F.xw + ((size_t)gr * F.W + gc) * C;
-                    r = __ldg(px);
-                    if (C == 3) {
-                        g = __ldg(px + 1);
-                        b = __ldg(px + 2);
+            for (int i = tid_e; i < kXPairs * kTC; i += kEpi) {
+                // pair j: tile rows 2 j - 1 and 2 j (rows outside the tile or the frame are 0)
+                const int j = i / kTC, tcol = i - j * kTC;
+                const int gc = c0 - kHalo + tcol;
+                uint2 px2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int tr = 2 * j - 1 + h, gr = r_band - kHalo + tr;
+                    float r = 0.f, g = 0.f, b = 0.f;
+                    if (tr >= 0 && tr < kTR && gr >= 0 && gr < F.H && gc >= 0 && gc < F.W) {
+                        const float *px = F.xw + ((size_t)gr * F.W + gc) * C;
+                        r = __ldg(px);
+                        if (C == 3) {
+                            g = __ldg(px + 1);
+                            b = __ldg(px + 2);
+                        }
                     }
+                    px2[h] = encode_px(r, g, b);
                 }
-                x16[i] = encode_px(r, g, b);
+                xp[i] = make_uint4(px2[0].x, px2[0].y, px2[1].x, px2[1].y);
             }
             ptx::named_bar(1, kEpi);
             for (int rp = 0; rp < npair; ++rp, ++pairs) {
-                // ---- beta of row 2 rp + grp into TMEM (groups 0 and 1) ----
-                if (grp < 2) {
-                    ok = __all_sync(0xffffffffu, wait_bar(BAR(kBStaged), pairs & 1, ctl, 32) && ok);
-                    if (ok) {
-                        const uint4 *src = sbeta + grp * (kBetaRow / 16) + col;
-#pragma unroll
-                        for (int q = 0; q < kGroups / 2; ++q) {
-                            const uint4 v0 = src[(2 * q) * kStrip], v1 = src[(2 * q + 1) * kStrip];
-                            const uint32_t u[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                            ptx::tmem_st8(lane_base + colBeta(grp) + 8 * q, u);
-                        }
-                        ptx::tmem_wait_st();
-                    }
-                    ptx::fence_before();
-                    __syncwarp();
-                    if (lane == 0) {
-                        ptx::mbar_arrive(BAR(kBFree));
-                        ptx::mbar_arrive(BAR(kBReady));
-                    }
-                }
+                copy_beta(pairs);
                 float acc[2][3];
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) acc[i][ch] = 0.f;
-                accumulate_pair<C>(p, x16, lane_base, col, rp, grp, bar0, uses, ok, ctl, lane, acc);
-                // ---- add the three groups' partial sums, write the row pair ----
+                accumulate_pair<C>(p, xp, lane_base, col, rp, grp, bar0, uses, ok, ctl, lane, acc);
+                // ---- add the four groups' partial sums, write the row pair ----
                 if (grp > 0) {
                     float *xc = xchg + (grp - 1) * kStrip * 6;
 #pragma unroll
@@ -392,7 +403,8 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                             float *o = F.y + ((size_t)orow * F.W + c0 + col) * C;
 #pragma unroll
                             for (int ch = 0; ch < C; ++ch)
-                                o[ch] = acc[i][ch] + xchg[col * 6 + i * 3 + ch] + xchg[kStrip * 6 + col * 6 + i * 3 + ch];
+                                o[ch] = acc[i][ch] + xchg[col * 6 + i * 3 + ch] + xchg[kStrip * 6 + col * 6 + i * 3 + ch] +
+                                        xchg[2 * kStrip * 6 + col * 6 + i * 3 + ch];
                         }
                     }
                 }

@@ -116,7 +116,7 @@ struct p2s_ctx {
     int use_graphs = 0;
     int blur_then_warp = 0;  // P2S_OPT_BLUR_THEN_WARP
     int field_method = 0;    // P2S_OPT_FIELD_METHOD: 0 Fourier filtering, 1 dense draw
-    int gather_split = 0;    // P2S_OPT_GATHER_SPLIT
+    int gather_split = 1;    // P2S_OPT_GATHER_SPLIT
     std::map<int, void *> dense_L;  // dense draw: FP32 Cholesky factors [n_kernels][n][n] by n
     void *arena = nullptr;
     size_t arena_bytes = 0;

@@ -109,6 +109,8 @@ def test_gather_band_16_equals_band_32():
     xs = [torch.from_numpy(x).cuda() for x in _frames(shapes)]
     a = _sim()
     b = _sim()
+    a.set_option("gather_split", 0)  # the band height belongs to the fused kernel
+    b.set_option("gather_split", 0)
     b.set_option("gather_band_rows", 16)
     ya = a.simulate(xs, [2.0, 3.0], [1, 2])
     yb = b.simulate(xs, [2.0, 3.0], [1, 2])
@@ -167,6 +169,7 @@ def test_split_gather_matches_oracle_and_fused(c):
     xs = _frames(shapes, c=c, first=2400)
     dr, seeds = [1.5, 3.0, 2.0, 5.0], [71, 72, 73, 74]
     fused = _sim()
+    fused.set_option("gather_split", 0)
     split = _sim()
     split.set_option("gather_split", 1)
     assert split.get_option("gather_split") == 1

@@ -72,7 +72,8 @@ def test_admission_holds_the_budget():
 
     sim = _sim()
     reqs = [(inputs.blob_image(96, 160, 3, 3100 + i), 1.0 + i, 8000 + i) for i in range(5)]
-    srv = p2s.Server(sim, hbm_budget_bytes=1_000_000, max_inflight=4, max_batch=8)
+    budget = 6_000_000
+    srv = p2s.Server(sim, hbm_budget_bytes=budget, max_inflight=4, max_batch=8)
     outs = [np.zeros_like(x) for x, _, _ in reqs]
     tickets = [srv.submit(x, dr, sd, o) for (x, dr, sd), o in zip(reqs, outs)]
     for t in tickets:
@@ -80,8 +81,10 @@ def test_admission_holds_the_budget():
     st = srv.stats()
     srv.close()
     assert st["completed"] == len(reqs)
-    assert st["peak_bytes"] <= 1_000_000
-    assert st["mean_batch"] == 1.0  # one 96 x 160 request holds ~0.73 MB of the 1 MB
+    assert st["peak_bytes"] <= budget
+    # one 96 x 160 request holds ~4.2 MB: frames, fields, and 224 B per pixel of 16-bit
+    # beta between the network and blur kernels; a second one does not fit
+    assert st["mean_batch"] == 1.0
 
 
 def test_request_larger_than_the_budget_is_refused():
