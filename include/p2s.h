@@ -219,7 +219,8 @@ p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
  *   P2S_OPT_GRAPH_INSTANTIATIONS, P2S_OPT_GRAPH_UPDATES  (read only) how many
  *       graphs were instantiated / updated in place so far.
  *   P2S_OPT_GATHER_BAND_ROWS  tile height of the fused tensor-core gather
- *       kernel: 16 or 32 output rows per 128-column tile (0 = default 32).
+ *       kernel (P2S_OPT_GATHER_SPLIT = 0): 16 or 32 output rows per 128-column
+ *       tile (0 = default 32).
  *   P2S_OPT_BLUR_THEN_WARP  1: p2s_simulate blurs the input first and applies
  *       the tilt warp to the blurred frame, the order of the collapsed model
  *       (Sec. 2.2: the turbulent PSF is a tilt-free PSF shifted by the tilt);
@@ -229,11 +230,12 @@ p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
  *       1 the dense draw f = chol(Sigma) w of the anchors' full (unwrapped)
  *       Gaussian correlation matrix, evaluated through its Kronecker factors
  *       L_y W L_x^T (at most 128 anchors per axis).
- *   P2S_OPT_GATHER_SPLIT  tensor-core gather form only.  0 (default): one
- *       fused kernel evaluates the network and the blur per tile, beta never
- *       leaves the SM.  1: the network kernel writes beta in its 16-bit
- *       operand layout (224 B per pixel) and a blur-only tensor-core kernel
- *       with three accumulating warps per TMEM lane quadrant reads it back.
+ *   P2S_OPT_GATHER_SPLIT  tensor-core gather form only.  0: one fused
+ *       kernel evaluates the network and the blur per tile, beta never leaves
+ *       the SM.  1 (default): the network kernel writes beta in its 16-bit
+ *       operand layout (224 B per pixel of scratch) and a blur-only
+ *       tensor-core kernel with four accumulating warps per TMEM lane
+ *       quadrant reads it back.
  *       Same rounding points (beta and H in 16 bits, x staged in FP16, FP32
  *       accumulation); results differ from the fused kernel only in the order
  *       of FP32 summation. */
