@@ -37,8 +37,8 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # ncu: blur_tc_scatter from one full 64-frame launch / 64; blur_tc_gather16 and net_tc from one 8-frame
 # launch / 8, their traffic being proportional to the frames); valid for the kernels as measured, see
 # profiles/
-DRAM_BYTES_PER_FRAME = {"blur_tc_scatter": 4268525824 / 64, "blur_tc_gather16": (495926272 + 20272384) / 8,
-                        "net_tc": (5707008 + 404963328) / 8}
+DRAM_BYTES_PER_FRAME = {"blur_tc_scatter": 4268525824 / 64, "blur_tc_gather16": (496815360 + 20606976) / 8,
+                        "net_tc": (5699584 + 404974336) / 8}
 
 
 def workload_name(precision: str, form: str) -> str:
