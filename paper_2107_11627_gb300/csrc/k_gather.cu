@@ -47,7 +47,8 @@ constexpr int kSlots = 2;
 constexpr int kGroups = 14;                       // beta16 k-groups
 constexpr int kGroupsEpi = 4;                     // accumulating groups of 4 warps
 constexpr int kEpi = 128 * kGroupsEpi;            // 512
-constexpr int kThreads = 64 + kEpi;               // 576
+constexpr int kThreads = 64 + kEpi + 32;          // 608: + the second MMA warp (row 1)
+constexpr int kMmaWarp1 = (64 + kEpi) / 32;       // 18
 constexpr int kXPairs = kTR / 2 + 1;              // x tile rows (2 j - 1, 2 j), j = 0 .. 32
 constexpr int kBetaRow = kGroups * kStrip * 16;   // 28,672 B per staged row
 
@@ -220,13 +221,13 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
         *abort_flag = 0;
         for (int i = 0; i < kSlots; ++i) {
             ptx::mbar_init(BAR(kFull0 + i), 1);
-            ptx::mbar_init(BAR(kEmpty0 + i), 1);
+            ptx::mbar_init(BAR(kEmpty0 + i), 2);  // one commit per MMA thread
         }
         ptx::mbar_init(BAR(kBStaged), 1);
         ptx::mbar_init(BAR(kBFree), 8);
         ptx::mbar_init(BAR(kBReady), 8);
         for (int i = 0; i < 2; ++i) {
-            ptx::mbar_init(BAR(kDFull0 + i), 1);
+            ptx::mbar_init(BAR(kDFull0 + i), 2);  // one commit per MMA thread
             ptx::mbar_init(BAR(kDEmpty0 + i), 4 * kGroupsEpi);
         }
         ptx::mbar_fence_init();
@@ -281,9 +282,12 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                 drain_bar(BAR(kFull0 + k % kSlots), (k / kSlots) & 1);
             if (pairs > 0) drain_bar(BAR(kBStaged), (pairs - 1) & 1);
         }
-    } else if (warp == 0) {
-        // ---------------- MMA issuer ----------------
+    } else if (warp == 0 || warp == kMmaWarp1) {
+        // ---------------- MMA issuers: warp 0 row 0, warp 18 row 1 ----------------
+        // One thread issues an MMA about every 76-100 cycles whatever its size; two
+        // threads in two warps, each on its own accumulator, keep the tensor core busy.
         if (lane == 0) {
+            const int row = warp == 0 ? 0 : 1;
             uint32_t it = 0, pairs = 0, uses[2] = {0, 0};
             for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
                 const int npair = n_pairs_of(tile);
@@ -301,13 +305,10 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                             const uint32_t idesc = (n == (uint32_t)kMainN) ? idesc_n96 : idesc_n48;
                             const uint64_t bd = ptx::smem_desc(sbase + kOffRing + slot * kSlot, n * 16, 128);
                             const uint64_t bstep = (uint64_t)(2 * n);
-                            const uint32_t d0 = tmem + colDB(h), d1 = d0 + kMainN;
-                            const uint32_t a0 = tmem + colBeta(0), a1 = tmem + colBeta(1);
+                            const uint32_t d = tmem + colDB(h) + row * kMainN, a = tmem + colBeta(row);
 #pragma unroll
-                            for (int ks = 0; ks < kKSteps; ++ks) {
-                                ptx::mma_ts(d0, a0 + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
-                                ptx::mma_ts(d1, a1 + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
-                            }
+                            for (int ks = 0; ks < kKSteps; ++ks)
+                                ptx::mma_ts(d, a + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
                         }
                         ptx::mma_commit(BAR(kEmpty0 + slot));
                         ptx::mma_commit(BAR(kDFull0 + h));
