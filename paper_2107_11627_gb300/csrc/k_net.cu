@@ -16,9 +16,10 @@
 // the same buffer), so a slot needs only the 128 TMEM columns of its D.  The
 // slot count is the largest that fits the weights and anchor rows in shared
 // memory (4 for FP16 weights at anchor spacing 8, 2 for the BF16 hi/lo pair).
-// Roles: warp 0 loads the weights once and issues the MMAs (one thread,
-// serving whichever slot is ready); four converting warps per slot, one per
-// TMEM lane quadrant.  A CTA takes a contiguous run of units ordered
+// Roles: one MMA-issuing thread per slot (warp 0 also loads the weights, warps
+// 4 NS + s issue for slots s >= 1): a single thread issues an MMA only every
+// 76-100 cycles, several threads keep the tensor core busy.  Four converting
+// warps per slot, one per TMEM lane quadrant (warps 1 .. 4 NS).  A CTA takes a contiguous run of units ordered
 // row-fastest within a 128-column block, so consecutive units share anchor
 // rows (L1 hits).  Every wait is bounded.
 #include <cuda_bf16.h>
@@ -40,7 +41,7 @@ using tcc::wait_bar;
 
 constexpr int kTile = 128;
 constexpr int kMaxSlots = 4;
-constexpr int kThreads = 32 + kMaxSlots * 128;  // warp 0 + four converting warps per slot
+constexpr int kThreads = kMaxSlots * 160;        // per slot: four converting warps and one MMA warp
 constexpr int kK1 = 48;                         // layer-1 depth: 33 modes padded
 constexpr int kGroups = 14;                     // beta16 k-groups of 8 (K padded to 112)
 constexpr int kABytes = kTile * 128 * 2;        // A operand of one slot: [16 k-groups][128 rows][16 B]
@@ -78,6 +79,9 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NS = p.nslots;
     Ctl ctl{abort_flag, p.status};
+    const int u_base = (int)blockIdx.x * p.per_cta;
+    const int n_local = max(0, min(p.per_cta, p.tiles_total - u_base));
+    const int n_issuers = min(NS, n_local);  // slots with work
 
     if (threadIdx.x == 0) {
         *abort_flag = 0;
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                 ptx::mbar_init(BAR(barA(s, L)), 4);
                 ptx::mbar_init(BAR(barD(s, L)), 1);
             }
-        ptx::mbar_init(BAR(kDone), 1);
+        ptx::mbar_init(BAR(kDone), n_issuers > 0 ? n_issuers : 1);
         ptx::mbar_fence_init();
     }
     for (int i = threadIdx.x; i < p.h1p + p.h2p; i += blockDim.x) sbias[i] = p.bias[i];
@@ -96,37 +100,27 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
     __syncthreads();
     ptx::fence_after();
     const uint32_t tmem = *tmem_holder;
-    const int u_base = (int)blockIdx.x * p.per_cta;
-    const int n_local = max(0, min(p.per_cta, p.tiles_total - u_base));
 
-    if (warp == 0) {
-        // ---------------- weights once, then the MMAs of whichever slot is ready ----------------
-        if (lane == 0 && n_local > 0) {
-            ptx::mbar_arrive_tx(BAR(kW), p.wbytes);
-            for (int i = 0; i < 3 * p.per; ++i)
-                ptx::bulk_g2s(sbase + p.item_soff[i], p.wstream + p.item_off[i], p.item_bytes[i], BAR(kW));
+    if (warp == 0 || warp > 4 * NS) {
+        // ---------------- MMA issuer of one slot (warp 0: slot 0, and the weights) ----------------
+        const int s = warp == 0 ? 0 : warp - 4 * NS;
+        if (lane == 0 && s < n_issuers) {
+            if (s == 0) {
+                ptx::mbar_arrive_tx(BAR(kW), p.wbytes);
+                for (int i = 0; i < 3 * p.per; ++i)
+                    ptx::bulk_g2s(sbase + p.item_soff[i], p.wstream + p.item_off[i], p.item_bytes[i], BAR(kW));
+            }
             const bool wok = wait_bar(BAR(kW), 0, ctl, 1);
             ptx::fence_after();
-            int js[kMaxSlots], Ls[kMaxSlots];
-#pragma unroll
-            for (int s = 0; s < kMaxSlots; ++s) {
-                js[s] = s;
-                Ls[s] = 0;
-            }
-            long long t0 = clock64();
-            for (;;) {
-                bool any = false, prog = false;
-#pragma unroll
-                for (int s = 0; s < kMaxSlots; ++s) {
-                    if (s >= NS || js[s] >= n_local) continue;
-                    any = true;
-                    const int L = Ls[s];
-                    const bool aborted = *abort_flag != 0;
-                    if (!aborted && !ptx::mbar_test(BAR(barA(s, L)), (uint32_t)(js[s] / NS) & 1u)) continue;
+            const uint32_t d = tmem + 128u * s;
+            const uint64_t ad = ptx::smem_desc(sbase + p.offA + s * kABytes, kTile * 16, 128);
+            for (int i = s; i < n_local; i += NS) {
+                const uint32_t ph = (uint32_t)(i / NS) & 1u;
+#pragma unroll 1
+                for (int L = 0; L < 3; ++L) {
+                    const bool rdy = wait_bar(BAR(barA(s, L)), ph, ctl, 2);
                     ptx::fence_after();
-                    if (!aborted && wok) {
-                        const uint32_t d = tmem + 128u * s;
-                        const uint64_t ad = ptx::smem_desc(sbase + p.offA + s * kABytes, kTile * 16, 128);
+                    if (rdy && wok) {
                         for (int w = 0; w < p.per; ++w) {
                             const int it = L * p.per + w;
                             const uint32_t n = p.item_n[it];
@@ -139,18 +133,6 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                         }
                     }
                     ptx::mma_commit(BAR(barD(s, L)));
-                    if (++Ls[s] == 3) {
-                        Ls[s] = 0;
-                        js[s] += NS;
-                    }
-                    prog = true;
-                }
-                if (!any) break;
-                if (prog) {
-                    t0 = clock64();
-                } else if (clock64() - t0 > 4000000000ll) {
-                    *abort_flag = 1;
-                    atomicOr(p.status, 2);
                 }
             }
             // every copy and MMA has completed before shared and tensor memory are released
@@ -404,10 +386,10 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
     ProfScope pr(ctx, st, "net_tc", 2.0 * macs * npx, npx * kGroups * 16.0);
     if (p.ab_fmt == 1) {
         P2S_CUDA(cudaFuncSetAttribute(net_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        net_kernel<1><<<grid, 32 + 128 * p.nslots, smem, st>>>(p);
+        net_kernel<1><<<grid, 160 * p.nslots, smem, st>>>(p);
     } else {
         P2S_CUDA(cudaFuncSetAttribute(net_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        net_kernel<0><<<grid, 32 + 128 * p.nslots, smem, st>>>(p);
+        net_kernel<0><<<grid, 160 * p.nslots, smem, st>>>(p);
     }
     P2S_CUDA(cudaGetLastError());
     return P2S_OK;
