@@ -63,7 +63,8 @@ constexpr int kHAll = kTaps * kTaps + 15;         // 1104 packed basis rows
 constexpr int kHSlot = 25600;                     // >= 14 * 114 * 16, 1024-aligned
 constexpr int kN = 48;
 constexpr int kDSlots = 10;
-constexpr int kThreads = 320;
+constexpr int kThreads = 352;  // + the second MMA warp (warp 10, row 1)
+constexpr int kMmaWarp1 = 10;
 constexpr int kEpi = 256;
 
 constexpr int kOffBeta = 0;                            // 4 rows (two pairs)
@@ -284,15 +285,15 @@ __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_const
         *abort_flag = 0;
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(BAR(kBFull + i), 1);
-            ptx::mbar_init(BAR(kBEmpty + i), 1);
+            ptx::mbar_init(BAR(kBEmpty + i), 2);  // one commit per MMA thread
             ptx::mbar_init(BAR(kHFull + i), 1);
-            ptx::mbar_init(BAR(kHEmpty + i), 1);
+            ptx::mbar_init(BAR(kHEmpty + i), 2);
         }
         for (int i = 0; i < kDSlots; ++i) {
             ptx::mbar_init(BAR(kDFull + i), 1);
             ptx::mbar_init(BAR(kDEmpty + i), 8);
         }
-        ptx::mbar_init(BAR(kDone), 1);
+        ptx::mbar_init(BAR(kDone), 2);
         ptx::mbar_fence_init();
     }
     if (warp == 0) ptx::tmem_alloc(ptx::smem_u32(tmem_holder), 512);
@@ -344,9 +345,12 @@ __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_const
             for (uint32_t k = pc > 2 ? pc - 2 : 0; k < pc; ++k) drain_bar(BAR(kBFull + (k & 1)), (k >> 1) & 1);
             for (uint32_t k = hc > 2 ? hc - 2 : 0; k < hc; ++k) drain_bar(BAR(kHFull + (k & 1)), (k >> 1) & 1);
         }
-    } else if (warp == 0) {
-        // ---------------- MMA issuer ----------------
+    } else if (warp == 0 || warp == kMmaWarp1) {
+        // ---------------- MMA issuers: warp 0 row 0, warp 10 row 1 ----------------
+        // One thread issues an MMA about every 76-100 cycles whatever its size; a
+        // thread per row, each on its own accumulators, keeps the tensor core busy.
         if (lane == 0) {
+            const int row = warp == 0 ? 0 : 1;
             const uint32_t idesc = ptx::idesc_f16(p.ab_fmt, kN);
             uint32_t pc = 0, hc = 0, dc = 0;
             for (int un = blockIdx.x; un < p.units; un += gridDim.x) {
@@ -357,29 +361,24 @@ __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_const
                     for (int j = 0; j < kChunks; ++j, ++hc) {
                         const uint32_t hslot = hc & 1;
                         const bool hok = wait_bar(BAR(kHFull + hslot), (hc >> 1) & 1, ctl, 8);
-                        // per tap column, the two rows' accumulators: their K-step chains are
-                        // interleaved so that no MMA waits on the previous step of its own D
+                        // per tap column, this row's accumulator (accumulator slots alternate
+                        // between the rows: row 0 even, row 1 odd)
                         for (int uu = 0; uu < kTxPerChunk; ++uu, dc += 2) {
                             const int tx = j * kTxPerChunk + uu;
-                            const uint32_t d0 = dc % kDSlots, d1 = (dc + 1) % kDSlots;
-                            const bool e0 = wait_bar(BAR(kDEmpty + d0), ((dc / kDSlots) & 1) ^ 1, ctl, 32);
-                            const bool e1 = wait_bar(BAR(kDEmpty + d1), (((dc + 1) / kDSlots) & 1) ^ 1, ctl, 32);
+                            const uint32_t dd = (dc + row) % kDSlots;
+                            const bool e = wait_bar(BAR(kDEmpty + dd), (((dc + row) / kDSlots) & 1) ^ 1, ctl, 32);
                             ptx::fence_after();
-                            if (bok && hok && e0 && e1) {
+                            if (bok && hok && e) {
                                 const uint64_t bd =
                                     ptx::smem_desc(sbase + kOffH + hslot * kHSlot + uu * kTaps * 16, kHRows * 16, 128);
-                                const uint32_t a0 = sbase + kOffBeta + (2 * bslot) * kBetaRow + (2 * kHalo - tx) * 16;
-                                const uint64_t ad0 = ptx::smem_desc(a0, kPos * 16, 128);
-                                const uint64_t ad1 = ptx::smem_desc(a0 + kBetaRow, kPos * 16, 128);
+                                const uint32_t a0 = sbase + kOffBeta + (2 * bslot + row) * kBetaRow + (2 * kHalo - tx) * 16;
+                                const uint64_t ad = ptx::smem_desc(a0, kPos * 16, 128);
 #pragma unroll
-                                for (int ks = 0; ks < kKSteps; ++ks) {
-                                    const uint64_t bk = bd + (uint64_t)(ks * 2 * kHRows);
-                                    ptx::mma_ss(tmem + d0 * kN, ad0 + (uint64_t)(ks * 2 * kPos), bk, idesc, ks > 0 ? 1u : 0u);
-                                    ptx::mma_ss(tmem + d1 * kN, ad1 + (uint64_t)(ks * 2 * kPos), bk, idesc, ks > 0 ? 1u : 0u);
-                                }
+                                for (int ks = 0; ks < kKSteps; ++ks)
+                                    ptx::mma_ss(tmem + dd * kN, ad + (uint64_t)(ks * 2 * kPos), bd + (uint64_t)(ks * 2 * kHRows),
+                                                idesc, ks > 0 ? 1u : 0u);
                             }
-                            ptx::mma_commit(BAR(kDFull + d0));
-                            ptx::mma_commit(BAR(kDFull + d1));
+                            ptx::mma_commit(BAR(kDFull + dd));
                         }
                         ptx::mma_commit(BAR(kHEmpty + hslot));
                     }
