@@ -63,8 +63,9 @@ constexpr int kHAll = kTaps * kTaps + 15;         // 1104 packed basis rows
 constexpr int kHSlot = 25600;                     // >= 14 * 114 * 16, 1024-aligned
 constexpr int kN = 48;
 constexpr int kDSlots = 10;
-constexpr int kThreads = 352;  // + the second MMA warp (warp 10, row 1)
+constexpr int kThreads = 416;  // + MMA warps 10, 11, 12
 constexpr int kMmaWarp1 = 10;
+constexpr int kIssuers = 4;    // (row, tap-column parity)
 constexpr int kEpi = 256;
 
 constexpr int kOffBeta = 0;                            // 4 rows (two pairs)
@@ -285,15 +286,15 @@ __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_const
         *abort_flag = 0;
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(BAR(kBFull + i), 1);
-            ptx::mbar_init(BAR(kBEmpty + i), 2);  // one commit per MMA thread
+            ptx::mbar_init(BAR(kBEmpty + i), kIssuers);  // one commit per MMA thread
             ptx::mbar_init(BAR(kHFull + i), 1);
-            ptx::mbar_init(BAR(kHEmpty + i), 2);
+            ptx::mbar_init(BAR(kHEmpty + i), kIssuers);
         }
         for (int i = 0; i < kDSlots; ++i) {
             ptx::mbar_init(BAR(kDFull + i), 1);
             ptx::mbar_init(BAR(kDEmpty + i), 8);
         }
-        ptx::mbar_init(BAR(kDone), 2);
+        ptx::mbar_init(BAR(kDone), kIssuers);
         ptx::mbar_fence_init();
     }
     if (warp == 0) ptx::tmem_alloc(ptx::smem_u32(tmem_holder), 512);
@@ -345,12 +346,15 @@ __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_const
             for (uint32_t k = pc > 2 ? pc - 2 : 0; k < pc; ++k) drain_bar(BAR(kBFull + (k & 1)), (k >> 1) & 1);
             for (uint32_t k = hc > 2 ? hc - 2 : 0; k < hc; ++k) drain_bar(BAR(kHFull + (k & 1)), (k >> 1) & 1);
         }
-    } else if (warp == 0 || warp == kMmaWarp1) {
-        // ---------------- MMA issuers: warp 0 row 0, warp 10 row 1 ----------------
-        // One thread issues an MMA about every 76-100 cycles whatever its size; a
-        // thread per row, each on its own accumulators, keeps the tensor core busy.
+    } else if (warp == 0 || warp >= kMmaWarp1) {
+        // ---------------- MMA issuers: warps 0, 10, 11, 12 ----------------
+        // One thread issues an MMA about every 76-100 cycles whatever its size; four
+        // threads, each on its own accumulators (row 0 / 1 x even / odd tap column),
+        // keep the tensor core busy.  13 warps leave 128 registers per thread (a few
+        // bytes of spills in the RGB accumulators), still faster than two issuers.
         if (lane == 0) {
-            const int row = warp == 0 ? 0 : 1;
+            const int who = warp == 0 ? 0 : warp - kMmaWarp1 + 1;  // 0..3
+            const int row = who & 1, par = who >> 1;
             const uint32_t idesc = ptx::idesc_f16(p.ab_fmt, kN);
             uint32_t pc = 0, hc = 0, dc = 0;
             for (int un = blockIdx.x; un < p.units; un += gridDim.x) {
@@ -365,6 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_const
                         // between the rows: row 0 even, row 1 odd)
                         for (int uu = 0; uu < kTxPerChunk; ++uu, dc += 2) {
                             const int tx = j * kTxPerChunk + uu;
+                            if ((tx & 1) != par) continue;
                             const uint32_t dd = (dc + row) % kDSlots;
                             const bool e = wait_bar(BAR(kDEmpty + dd), (((dc + row) / kDSlots) & 1) ^ 1, ctl, 32);
                             ptx::fence_after();
