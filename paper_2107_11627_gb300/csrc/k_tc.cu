@@ -47,7 +47,8 @@ constexpr int kChunks = kMainChunks + 1;       // + the last tap row
 constexpr int kLastN = 48;
 constexpr int kSlot = 32768;
 constexpr int kSlots = 3;
-constexpr int kThreads = 320;
+constexpr int kThreads = 352;  // + the second MMA warp (warp 10, row 1)
+constexpr int kMmaWarp1 = 10;
 constexpr int kEpi = 256;
 
 // tensor-memory column map (512 columns allocated)
@@ -141,17 +142,17 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
         *abort_flag = 0;
         for (int i = 0; i < kSlots; ++i) {
             ptx::mbar_init(BAR(kFull0 + i), 1);
-            ptx::mbar_init(BAR(kEmpty0 + i), 1);
+            ptx::mbar_init(BAR(kEmpty0 + i), 2);  // one commit per MMA thread
         }
         ptx::mbar_init(BAR(kA1b), 8);
-        ptx::mbar_init(BAR(kD1b), 1);
+        ptx::mbar_init(BAR(kD1b), 2);
         ptx::mbar_init(BAR(kA2b), 8);
-        ptx::mbar_init(BAR(kD2b), 1);
+        ptx::mbar_init(BAR(kD2b), 2);
         ptx::mbar_init(BAR(kA3b), 8);
-        ptx::mbar_init(BAR(kD3b), 1);
+        ptx::mbar_init(BAR(kD3b), 2);  // D barriers: one commit per MMA thread
         ptx::mbar_init(BAR(kBetab), 8);
-        ptx::mbar_init(BAR(kDFull0), 1);
-        ptx::mbar_init(BAR(kDFull0 + 1), 1);
+        ptx::mbar_init(BAR(kDFull0), 2);
+        ptx::mbar_init(BAR(kDFull0 + 1), 2);
         ptx::mbar_init(BAR(kDEmpty0), 8);
         ptx::mbar_init(BAR(kDEmpty0 + 1), 8);
         ptx::mbar_fence_init();
@@ -197,9 +198,12 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
             for (uint32_t k = (it > (uint32_t)kSlots ? it - kSlots : 0); k < it; ++k)
                 drain_bar(BAR(kFull0 + k % kSlots), (k / kSlots) & 1);
         }
-    } else if (warp == 0) {
-        // ---------------- MMA issuer ----------------
+    } else if (warp == 0 || warp == kMmaWarp1) {
+        // ---------------- MMA issuers: warp 0 row 0, warp 10 row 1 ----------------
+        // One thread issues an MMA about every 76-100 cycles whatever its size; a
+        // thread per row, each on its own accumulators, keeps the tensor core busy.
         if (lane == 0) {
+            const int row = warp == 0 ? 0 : 1;
             uint32_t it = 0, pairs = 0, uses[2] = {0, 0};
             // next ring item: wait until it has landed; returns its shared address (0 if aborted)
             auto take = [&](uint32_t &slot) -> uint32_t {
@@ -231,13 +235,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                                     const int ksteps = (int)itm.k / 16;
                                     const uint64_t bd = ptx::smem_desc(sa, itm.n * 16, 128);
                                     const uint64_t bstep = (uint64_t)(2 * itm.n);  // 2 core-matrix columns, 16-byte units
-                                    const uint32_t d0 = tmem + d_reg[L][0], d1 = tmem + d_reg[L][1];
-                                    const uint32_t a0 = tmem + a_reg[L][0], a1 = tmem + a_reg[L][1];
-                                    for (int ks = 0; ks < ksteps; ++ks) {
-                                        const uint32_t acc = (w > 0 || ks > 0) ? 1u : 0u;
-                                        ptx::mma_ts(d0, a0 + ks * 8, bd + ks * bstep, idesc, acc);
-                                        ptx::mma_ts(d1, a1 + ks * 8, bd + ks * bstep, idesc, acc);
-                                    }
+                                    const uint32_t d = tmem + d_reg[L][row], a = tmem + a_reg[L][row];
+                                    for (int ks = 0; ks < ksteps; ++ks)
+                                        ptx::mma_ts(d, a + ks * 8, bd + ks * bstep, idesc, (w > 0 || ks > 0) ? 1u : 0u);
                                 }
                                 ptx::mma_commit(BAR(kEmpty0 + slot));
                             }
@@ -258,13 +258,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                                 const uint32_t idesc = (n == (uint32_t)kMainN) ? idesc_n96 : idesc_n48;
                                 const uint64_t bd = ptx::smem_desc(sa, n * 16, 128);
                                 const uint64_t bstep = (uint64_t)(2 * n);
-                                const uint32_t d0 = tmem + colDB(h), d1 = d0 + kMainN;
-                                const uint32_t a0 = tmem + colBeta(0), a1 = tmem + colBeta(1);
+                                const uint32_t d = tmem + colDB(h) + row * kMainN, a = tmem + colBeta(row);
 #pragma unroll
-                                for (int ks = 0; ks < kKSteps; ++ks) {
-                                    ptx::mma_ts(d0, a0 + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
-                                    ptx::mma_ts(d1, a1 + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
-                                }
+                                for (int ks = 0; ks < kKSteps; ++ks)
+                                    ptx::mma_ts(d, a + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
                             }
                             ptx::mma_commit(BAR(kEmpty0 + slot));
                             ptx::mma_commit(BAR(kDFull0 + h));
