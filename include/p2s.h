@@ -144,9 +144,13 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
                         const unsigned long long *seeds, const p2s_image *out, void *stream);
 
 /* As p2s_simulate, but frames[i].data and out[i].data are HOST pointers: the
- * call stages them through device buffers owned by the context (host->device
- * copy, path, device->host copy, all on `stream`) and returns when out[] is
- * written.  Pinned host memory gives full copy bandwidth. */
+ * call stages them through device buffers (host->device copy, path,
+ * device->host copy) and returns when out[] is written.  From 32 frames on,
+ * the frames go in chunks of at least 16 (at most 4 chunks): a chunk's
+ * host->device copy overlaps the path of the chunk before it and its
+ * device->host copy the path of the chunk after, on two copy streams owned by
+ * the context; the path runs on `stream`.  Results equal p2s_simulate's.
+ * Pinned host memory gives full copy bandwidth and overlap. */
 p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
                              const unsigned long long *seeds, const p2s_image *out, void *stream);
 

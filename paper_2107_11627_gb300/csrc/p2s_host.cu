@@ -363,6 +363,9 @@ void p2s_destroy(p2s_ctx *ctx) {
         if (kv.second) cudaGraphExecDestroy(kv.second);
     cudaFree(ctx->arena);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaStream_t cs : ctx->copy_stream)
+        if (cs) cudaStreamDestroy(cs);
+    for (cudaEvent_t e : ctx->host_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->cap_ev)
         if (e) cudaEventDestroy(e);
     delete ctx;
@@ -1059,10 +1062,26 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
     p2s_status st = validate_simulate(ctx, frames, n, d_over_r0, seeds, out);
     if (st != P2S_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    // The frames go in chunks: chunk k's host->device copy (copy stream 0) overlaps the
+    // path of chunk k - 1 (the caller's stream), whose device->host copy (copy stream 1)
+    // overlaps the path of chunk k + 1.  Chunks of at least 16 frames keep the persistent
+    // launches full; at most 4 chunks.
+    const int nch = n >= 32 ? std::min(4, n / 16) : 1;
+    for (int i = 0; i < 2; ++i)
+        if (!ctx->copy_stream[i]) P2S_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream[i], cudaStreamNonBlocking));
+    while ((int)ctx->host_ev.size() < 2 * nch + 2) {
+        cudaEvent_t e;
+        P2S_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->host_ev.push_back(e);
+    }
+    cudaEvent_t ev_alloc = ctx->host_ev[0], ev_done = ctx->host_ev[1];
+    cudaStream_t cin = ctx->copy_stream[0], cout = ctx->copy_stream[1];
     size_t total = 0;
     for (int i = 0; i < n; ++i) total += 2 * (((size_t)frames[i].H * frames[i].W * frames[i].C * 4 + 255) & ~(size_t)255);
     char *buf = nullptr;
     P2S_CUDA(cudaMallocAsync((void **)&buf, total + 256, s));
+    P2S_CUDA(cudaEventRecord(ev_alloc, s));
+    P2S_CUDA(cudaStreamWaitEvent(cin, ev_alloc, 0));
     std::vector<p2s_image> din(n), dout(n);
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
@@ -1073,20 +1092,42 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
         dout[i] = out[i];
         dout[i].data = (float *)(buf + off);
         off += (bytes + 255) & ~(size_t)255;
-        if (cudaMemcpyAsync(din[i].data, frames[i].data, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-            cudaFreeAsync(buf, s);
-            set_error("host->device copy failed");
-            return P2S_ECUDA;
+    }
+    auto chunk_begin = [&](int k) { return (int)((long long)n * k / nch); };
+    // all host->device copies, chunk by chunk, each chunk's end marked
+    for (int k = 0; k < nch && st == P2S_OK; ++k) {
+        for (int i = chunk_begin(k); i < chunk_begin(k + 1); ++i) {
+            const size_t bytes = (size_t)frames[i].H * frames[i].W * frames[i].C * 4;
+            if (cudaMemcpyAsync(din[i].data, frames[i].data, bytes, cudaMemcpyHostToDevice, cin) != cudaSuccess) {
+                set_error("host->device copy failed");
+                st = P2S_ECUDA;
+                break;
+            }
+        }
+        if (st == P2S_OK && cudaEventRecord(ctx->host_ev[2 + 2 * k], cin) != cudaSuccess) st = P2S_ECUDA;
+    }
+    // the path per chunk on the caller's stream, each chunk's results copied back
+    for (int k = 0; k < nch && st == P2S_OK; ++k) {
+        const int i0 = chunk_begin(k), i1 = chunk_begin(k + 1);
+        P2S_CUDA(cudaStreamWaitEvent(s, ctx->host_ev[2 + 2 * k], 0));
+        st = p2s_simulate(ctx, din.data() + i0, i1 - i0, d_over_r0 + i0, seeds + i0, dout.data() + i0, stream);
+        if (st != P2S_OK) break;
+        P2S_CUDA(cudaEventRecord(ctx->host_ev[3 + 2 * k], s));
+        P2S_CUDA(cudaStreamWaitEvent(cout, ctx->host_ev[3 + 2 * k], 0));
+        for (int i = i0; i < i1; ++i) {
+            const size_t bytes = (size_t)out[i].H * out[i].W * out[i].C * 4;
+            if (cudaMemcpyAsync(out[i].data, dout[i].data, bytes, cudaMemcpyDeviceToHost, cout) != cudaSuccess) {
+                set_error("device->host copy failed");
+                st = P2S_ECUDA;
+                break;
+            }
         }
     }
-    st = p2s_simulate(ctx, din.data(), n, d_over_r0, seeds, dout.data(), stream);
-    for (int i = 0; st == P2S_OK && i < n; ++i) {
-        const size_t bytes = (size_t)out[i].H * out[i].W * out[i].C * 4;
-        if (cudaMemcpyAsync(out[i].data, dout[i].data, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
-            set_error("device->host copy failed");
-            st = P2S_ECUDA;
-        }
-    }
+    // the buffers are released on the caller's stream once every copy is done
+    cudaEventRecord(ev_done, cout);
+    cudaStreamWaitEvent(s, ev_done, 0);
+    cudaEventRecord(ev_done, cin);
+    cudaStreamWaitEvent(s, ev_done, 0);
     cudaFreeAsync(buf, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && st == P2S_OK) {
         set_error("stream synchronize failed: %s", cudaGetErrorString(cudaGetLastError()));

@@ -122,6 +122,9 @@ struct p2s_ctx {
     size_t arena_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t cap_ev[2] = {nullptr, nullptr};
+    // p2s_simulate_host: copy streams (host->device, device->host) and per-chunk events
+    cudaStream_t copy_stream[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> host_ev;
     std::map<std::string, cudaGraphExec_t> graphs;
     long long graph_updates = 0, graph_instantiations = 0;
     // kernel timing

@@ -207,3 +207,19 @@ def test_split_gather_blur_then_warp_and_graphs():
                                     cfg2()["layers"], CorrParams(8, (16.0,)), (33, 33), form="gather",
                                     order="blur_warp")
         assert rel(ya[i].cpu().numpy(), ref.y) < TOL_BF16
+
+
+def test_host_entry_point_pipelines_chunks_bit_exact():
+    """p2s_simulate_host splits >= 32 frames into chunks whose copies overlap the path of the
+    neighbouring chunks; every frame must equal the device-buffer call (the gather is
+    batch-invariant), including a chunk boundary inside a run of equal shapes."""
+    sim = _sim()
+    shapes = [(48, 64)] * 20 + [(40, 72)] * 17 + [(64, 48)] * 3
+    xs = _frames(shapes, first=2600)
+    dr = [0.5 + 0.1 * i for i in range(len(xs))]
+    seeds = [900 + i for i in range(len(xs))]
+    yd = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
+    yh = sim.simulate_host(xs, dr, seeds)
+    sim.check()
+    for i in range(len(xs)):
+        assert np.array_equal(yh[i], yd[i].cpu().numpy()), i
