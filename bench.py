@@ -33,12 +33,11 @@ N_FRAMES, HW, CH, K, TAPS, N_DICT = 64, 512, 3, 100, 33, 50_000
 DIMS = [33, 128, 128, 100]
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-# DRAM bytes per 512x512 RGB frame of each kernel (dram__bytes_read.sum + dram__bytes_write.sum under
-# ncu: blur_tc_scatter from one full 64-frame launch / 64; blur_tc_gather16 and net_tc from one 8-frame
-# launch / 8, their traffic being proportional to the frames); valid for the kernels as measured, see
-# profiles/
-DRAM_BYTES_PER_FRAME = {"blur_tc_scatter": 4268525824 / 64, "blur_tc_gather16": (496815360 + 20606976) / 8,
-                        "net_tc": (5699584 + 404974336) / 8}
+# DRAM bytes per 512x512 RGB frame of each kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
+# 8-frame launch under ncu, divided by 8: the traffic is proportional to the frames, 16-bit beta and
+# x_w exceeding L2 already at 8 frames); valid for the kernels as measured, see profiles/
+DRAM_BYTES_PER_FRAME = {"blur_tc_scatter": (505780480 + 20903424) / 8, "blur_tc_gather16": (495836160 + 20237312) / 8,
+                        "net_tc": (5714944 + 404977920) / 8}
 
 
 def workload_name(precision: str, form: str) -> str:
