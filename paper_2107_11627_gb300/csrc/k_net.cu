@@ -251,11 +251,16 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                         const int g = c32 / 8 + q;
                         if (g < kGroups) {
                             float v[8];
+                            if (8 * g + 8 <= p.K) {  // every group below K: the values as they are
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const int k = 8 * g + j;
-                                v[j] = k < p.K ? __uint_as_float(d[8 * q + j])
-                                               : ((p.ones && (k == p.K || k == p.K + 1)) ? 1.0f : 0.0f);
+                                for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(d[8 * q + j]);
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) {
+                                    const int k = 8 * g + j;
+                                    v[j] = k < p.K ? __uint_as_float(d[8 * q + j])
+                                                   : ((p.ones && (k == p.K || k == p.K + 1)) ? 1.0f : 0.0f);
+                                }
                             }
                             uint4 w4;
                             w4.x = pack2(v[0], v[1], FMT);
