@@ -220,12 +220,12 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
 #pragma unroll
                         for (int j = 0; j < 2; ++j) {
                             const float4 bb = bv[2 * g + j];
-                            const float h0 = fmaxf(__uint_as_float(d[8 * g + 4 * j]) + bb.x, 0.f);
-                            const float h1 = fmaxf(__uint_as_float(d[8 * g + 4 * j + 1]) + bb.y, 0.f);
-                            const float h2 = fmaxf(__uint_as_float(d[8 * g + 4 * j + 2]) + bb.z, 0.f);
-                            const float h3 = fmaxf(__uint_as_float(d[8 * g + 4 * j + 3]) + bb.w, 0.f);
-                            w4[2 * j] = pack2(h0, h1, FMT);
-                            w4[2 * j + 1] = pack2(h2, h3, FMT);
+                            const float h0 = __uint_as_float(d[8 * g + 4 * j]) + bb.x;
+                            const float h1 = __uint_as_float(d[8 * g + 4 * j + 1]) + bb.y;
+                            const float h2 = __uint_as_float(d[8 * g + 4 * j + 2]) + bb.z;
+                            const float h3 = __uint_as_float(d[8 * g + 4 * j + 3]) + bb.w;
+                            w4[2 * j] = tcc::pack2_relu(h0, h1, FMT);  // ReLU in the conversion
+                            w4[2 * j + 1] = tcc::pack2_relu(h2, h3, FMT);
                         }
                         *(uint4 *)(abuf + (c32 / 8 + g) * (kTile * 16) + m * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
                     }

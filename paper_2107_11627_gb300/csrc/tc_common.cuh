@@ -21,6 +21,17 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int fmt) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// max(a, 0), max(b, 0) -> one 32-bit word, in one conversion instruction (the
+// value max(x, 0) rounded as pack2 rounds it)
+__device__ __forceinline__ uint32_t pack2_relu(float a, float b, int fmt) {
+    uint32_t r;
+    if (fmt == 1)
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    else
+        asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+
 struct Ctl {
     volatile int *abort;
     int *status;
