@@ -220,10 +220,11 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
 #pragma unroll
                         for (int j = 0; j < 2; ++j) {
                             const float4 bb = bv[2 * g + j];
-                            const float h0 = __uint_as_float(d[8 * g + 4 * j]) + bb.x;
-                            const float h1 = __uint_as_float(d[8 * g + 4 * j + 1]) + bb.y;
-                            const float h2 = __uint_as_float(d[8 * g + 4 * j + 2]) + bb.z;
-                            const float h3 = __uint_as_float(d[8 * g + 4 * j + 3]) + bb.w;
+                            float h0, h1, h2, h3;
+                            tcc::add2(__uint_as_float(d[8 * g + 4 * j]), __uint_as_float(d[8 * g + 4 * j + 1]), bb.x,
+                                      bb.y, h0, h1);
+                            tcc::add2(__uint_as_float(d[8 * g + 4 * j + 2]), __uint_as_float(d[8 * g + 4 * j + 3]),
+                                      bb.z, bb.w, h2, h3);
                             w4[2 * j] = tcc::pack2_relu(h0, h1, FMT);  // ReLU in the conversion
                             w4[2 * j + 1] = tcc::pack2_relu(h2, h3, FMT);
                         }

@@ -359,9 +359,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
                             uint32_t u[16];
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
-                                const float h0 = fmaxf(__uint_as_float(d[2 * j]) + sbias[boff[L] + 32 * q + 2 * j], 0.f);
-                                const float h1 = fmaxf(__uint_as_float(d[2 * j + 1]) + sbias[boff[L] + 32 * q + 2 * j + 1], 0.f);
-                                u[j] = pack2(h0, h1, p.ab_fmt);
+                                const float h0 = __uint_as_float(d[2 * j]) + sbias[boff[L] + 32 * q + 2 * j];
+                                const float h1 = __uint_as_float(d[2 * j + 1]) + sbias[boff[L] + 32 * q + 2 * j + 1];
+                                u[j] = tcc::pack2_relu(h0, h1, p.ab_fmt);  // ReLU in the conversion
                             }
                             const uint32_t (&u0)[8] = *reinterpret_cast<const uint32_t(*)[8]>(&u[0]);
                             const uint32_t (&u1)[8] = *reinterpret_cast<const uint32_t(*)[8]>(&u[8]);

@@ -21,6 +21,14 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int fmt) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// (a0 + b0, a1 + b1) as one packed FP32 pair add (each sum rounded as a plain add)
+__device__ __forceinline__ void add2(float a0, float a1, float b0, float b1, float &s0, float &s1) {
+    asm("{\n.reg .b64 p, q, r;\nmov.b64 p, {%2, %3};\nmov.b64 q, {%4, %5};\nadd.rn.f32x2 r, p, q;\n"
+        "mov.b64 {%0, %1}, r;\n}\n"
+        : "=f"(s0), "=f"(s1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 // max(a, 0), max(b, 0) -> one 32-bit word, in one conversion instruction (the
 // value max(x, 0) rounded as pack2 rounds it)
 __device__ __forceinline__ uint32_t pack2_relu(float a, float b, int fmt) {
