@@ -156,13 +156,14 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint4 *xp
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
                     const float a = __uint_as_float(g0[t]), bb = __uint_as_float(g1[t]);
-                    acc[0][0] = fmaf(a, wr[NT - 1 - t], acc[0][0]);
-                    acc[1][0] = fmaf(bb, wr[NT - t], acc[1][0]);
-                    if (C == 3) {
-                        acc[0][1] = fmaf(a, wg[NT - 1 - t], acc[0][1]);
+                    if (C == 3) {  // (R, G) as one packed FMA per output row
+                        tcc::fma2_bcast(a, wr[NT - 1 - t], wg[NT - 1 - t], acc[0][0], acc[0][1]);
+                        tcc::fma2_bcast(bb, wr[NT - t], wg[NT - t], acc[1][0], acc[1][1]);
                         acc[0][2] = fmaf(a, wb[NT - 1 - t], acc[0][2]);
-                        acc[1][1] = fmaf(bb, wg[NT - t], acc[1][1]);
                         acc[1][2] = fmaf(bb, wb[NT - t], acc[1][2]);
+                    } else {
+                        acc[0][0] = fmaf(a, wr[NT - 1 - t], acc[0][0]);
+                        acc[1][0] = fmaf(bb, wr[NT - t], acc[1][0]);
                     }
                 }
             }

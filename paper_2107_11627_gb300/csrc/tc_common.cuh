@@ -29,6 +29,14 @@ __device__ __forceinline__ void add2(float a0, float a1, float b0, float b1, flo
         : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
+// (c0, c1) += (a, a) * (b0, b1) as one packed FP32 pair FMA (each lane rounded as fmaf)
+__device__ __forceinline__ void fma2_bcast(float a, float b0, float b1, float &c0, float &c1) {
+    asm("{\n.reg .b64 p, q, r;\nmov.b64 p, {%2, %2};\nmov.b64 q, {%3, %4};\nmov.b64 r, {%0, %1};\n"
+        "fma.rn.f32x2 r, p, q, r;\nmov.b64 {%0, %1}, r;\n}\n"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a), "f"(b0), "f"(b1));
+}
+
 // max(a, 0), max(b, 0) -> one 32-bit word, in one conversion instruction (the
 // value max(x, 0) rounded as pack2 rounds it)
 __device__ __forceinline__ uint32_t pack2_relu(float a, float b, int fmt) {
