@@ -221,10 +221,17 @@ __device__ void accumulate(const Params &p, uint8_t *sm, uint32_t bar0, uint32_t
 #pragma unroll
                     for (int t = 0; t < NT; ++t) {
                         const float ga = __uint_as_float(a[t]), gb = __uint_as_float(b[t]);
+                        if (C == 3) {  // (R, G) as one packed FMA per source row
+                            tcc::fma2_bcast(ga, xv0[0], xv0[1], acc[t][0], acc[t][1]);
+                            tcc::fma2_bcast(gb, xv1[0], xv1[1], acc[t + 1][0], acc[t + 1][1]);
+                            acc[t][C - 1] = fmaf(ga, xv0[C - 1], acc[t][C - 1]);
+                            acc[t + 1][C - 1] = fmaf(gb, xv1[C - 1], acc[t + 1][C - 1]);
+                        } else {
 #pragma unroll
-                        for (int ch = 0; ch < C; ++ch) {
-                            acc[t][ch] = fmaf(ga, xv0[ch], acc[t][ch]);
-                            acc[t + 1][ch] = fmaf(gb, xv1[ch], acc[t + 1][ch]);
+                            for (int ch = 0; ch < C; ++ch) {
+                                acc[t][ch] = fmaf(ga, xv0[ch], acc[t][ch]);
+                                acc[t + 1][ch] = fmaf(gb, xv1[ch], acc[t + 1][ch]);
+                            }
                         }
                     }
                 }
