@@ -59,7 +59,8 @@ constexpr int kOffRing = 0;
 constexpr int kOffX = kOffRing + kSlots * kSlot;           // uint4 [kXPairs][kTC]: two FP16 RGB pixels
 constexpr int kOffBeta = kOffX + kXPairs * kTC * 16;       // [2 rows][14][128][16 B]
 constexpr int kOffXchg = kOffBeta + 2 * kBetaRow;          // float [3][128][6]
-enum Bar { kFull0 = 0, kEmpty0 = 2, kBStaged = 4, kBFree = 5, kBReady = 6, kDFull0 = 7, kDEmpty0 = 9, kNBar = 11 };
+enum Bar { kFull0 = 0, kEmpty0 = 2, kBStaged = 4, kBFree = 5, kBetaIn0 = 6, kPairDone0 = 8, kDFull0 = 10, kDEmpty0 = 12,
+           kNBar = 14 };
 constexpr int kOffBar = kOffXchg + (kGroupsEpi - 1) * kStrip * 6 * 4;
 constexpr int kOffMisc = kOffBar + kNBar * 8;
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;
@@ -209,7 +210,6 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = ptx::smem_u32(sm);
     uint4 *xp = (uint4 *)(sm + kOffX);
-    const uint4 *sbeta = (const uint4 *)(sm + kOffBeta);
     float *xchg = (float *)(sm + kOffXchg);
     const uint32_t bar0 = sbase + kOffBar;
     uint32_t *tmem_holder = (uint32_t *)(sm + kOffMisc);
@@ -225,8 +225,11 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
             ptx::mbar_init(BAR(kEmpty0 + i), 2);  // one commit per MMA thread
         }
         ptx::mbar_init(BAR(kBStaged), 1);
-        ptx::mbar_init(BAR(kBFree), 8);
-        ptx::mbar_init(BAR(kBReady), 8);
+        ptx::mbar_init(BAR(kBFree), 2);  // one commit per MMA thread
+        for (int r = 0; r < 2; ++r) {
+            ptx::mbar_init(BAR(kBetaIn0 + r), 1);
+            ptx::mbar_init(BAR(kPairDone0 + r), 1);
+        }
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(BAR(kDFull0 + i), 2);  // one commit per MMA thread
             ptx::mbar_init(BAR(kDEmpty0 + i), 4 * kGroupsEpi);
@@ -293,7 +296,21 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
             for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
                 const int npair = n_pairs_of(tile);
                 for (int rp = 0; rp < npair; ++rp, ++pairs) {
-                    const bool brdy = wait_bar(BAR(kBReady), pairs & 1, ctl, 8);
+                    // this row's beta into TMEM by tcgen05.cp, once the row's MMAs of the
+                    // previous pair are done with it: no accumulating warp is involved, so
+                    // the pair's first MMAs need not wait for the previous pair's tap sums
+                    if (pairs > 0) wait_bar(BAR(kPairDone0 + row), (pairs - 1) & 1, ctl, 8);
+                    const bool staged = wait_bar(BAR(kBStaged), pairs & 1, ctl, 8);
+                    ptx::fence_after();
+                    if (staged) {
+#pragma unroll
+                        for (int g = 0; g < kGroups; ++g)
+                            ptx::tmem_cp_128x128b(tmem + colBeta(row) + 4 * g,
+                                                  ptx::smem_desc(sbase + kOffBeta + row * kBetaRow + g * kStrip * 16, 16, 128));
+                    }
+                    ptx::mma_commit(BAR(kBFree));
+                    ptx::mma_commit(BAR(kBetaIn0 + row));
+                    const bool brdy = staged && wait_bar(BAR(kBetaIn0 + row), pairs & 1, ctl, 8);
                     ptx::fence_after();
                     for (int c = 0; c < kChunks; ++c, ++it) {
                         const int h = c & 1;
@@ -315,6 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                         ptx::mma_commit(BAR(kDFull0 + h));
                         ++uses[h];
                     }
+                    ptx::mma_commit(BAR(kPairDone0 + row));
                 }
             }
         }
@@ -328,28 +346,6 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
         const int tid_e = threadIdx.x - 64;
         uint32_t pairs = 0, uses = 0;
         bool ok = true;
-        // beta of row 2 rp + grp of pair number k (this CTA's count) into TMEM: groups 0 and 1;
-        // the MMAs of the pair wait for it, the producer then stages the next pair's
-        auto copy_beta = [&](uint32_t k) {
-            if (grp >= 2) return;
-            ok = __all_sync(0xffffffffu, wait_bar(BAR(kBStaged), k & 1, ctl, 32) && ok);
-            if (ok) {
-                const uint4 *src = sbeta + grp * (kBetaRow / 16) + col;
-#pragma unroll
-                for (int q = 0; q < kGroups / 2; ++q) {
-                    const uint4 v0 = src[(2 * q) * kStrip], v1 = src[(2 * q + 1) * kStrip];
-                    const uint32_t u[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                    ptx::tmem_st8(lane_base + colBeta(grp) + 8 * q, u);
-                }
-                ptx::tmem_wait_st();
-            }
-            ptx::fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                ptx::mbar_arrive(BAR(kBFree));
-                ptx::mbar_arrive(BAR(kBReady));
-            }
-        };
         for (int tile = blockIdx.x; tile < p.tiles_total; tile += gridDim.x) {
             const int f = frame_of(p, tile);
             const Frame &F = p.fr[f];
@@ -381,7 +377,6 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
             }
             ptx::named_bar(1, kEpi);
             for (int rp = 0; rp < npair; ++rp, ++pairs) {
-                copy_beta(pairs);
                 float acc[2][3];
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
