@@ -188,7 +188,9 @@ p2s_status p2s_stage_mlp16(p2s_ctx *ctx, int H, int W, const float *alpha, void 
 
 /* Step 5 alone: y = blur of x_w with per-pixel weights beta (device float32
  * [H][W][K]) in the context's form and precision (beta is rounded to the
- * operand type first). */
+ * operand type first).  FP16 / BF16 gather contexts run the same blur kernel
+ * as p2s_simulate (P2S_OPT_GATHER_SPLIT): with the option set, beta is first
+ * packed into the 16-bit operand layout in stream-ordered scratch. */
 p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, const p2s_image *out,
                           void *stream);
 

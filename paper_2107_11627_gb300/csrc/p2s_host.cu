@@ -624,6 +624,18 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
         FieldGeom g;
         if ((st = geometry(ctx, xw->H, xw->W, &g)) != P2S_OK) return st;
         const TcFrame f{xw->data, out->data, nullptr, xw->H, xw->W, g.Ah, g.Aw, 0, 0, 0};
+        if (ctx->gather_split) {
+            // the kernel p2s_simulate runs: beta in the 16-bit operand layout (its k >= K
+            // entries 0, so the folded bias rows add nothing: beta here includes the bias)
+            cudaStream_t s = (cudaStream_t)stream;
+            void *b16 = nullptr;
+            P2S_CUDA(cudaMallocAsync(&b16, beta16_bytes(xw->H, xw->W, 1), s));
+            st = launch_pack16(ctx, xw->H, xw->W, 1, beta, b16, s);
+            const void *bp[1] = {b16};
+            if (st == P2S_OK) st = launch_gather_split(ctx, &f, bp, 1, xw->C, ctx->d_status, s);
+            cudaFreeAsync(b16, s);
+            return st;
+        }
         return launch_tc(ctx, kTcBlurOnly, &f, 1, xw->C, beta, nullptr, ctx->d_status, (cudaStream_t)stream);
     }
     if (ctx->form == P2S_FFT) return launch_blur_fft(ctx, xw->H, xw->W, xw->C, 1, ip, beta, op, (cudaStream_t)stream);

@@ -49,10 +49,14 @@ def test_tc_network_stage(prec, h, w):
     assert rel(beta, ref) < TOL_BF16, rel(beta, ref)
 
 
+@pytest.mark.parametrize("split", [1, 0])
 @pytest.mark.parametrize("c", [3, 1])
 @pytest.mark.parametrize("h,w", [(40, 130), (33, 64), (1, 1), (70, 300)])
-def test_tc_blur_stage_fp16(c, h, w):
+def test_tc_blur_stage_fp16(c, h, w, split):
+    """Both gather kernels: the blur-only one fed by the network kernel's 16-bit beta
+    (split = 1, the default) and the fused one (split = 0)."""
     sim = _sim("fp16")
+    sim.set_option("gather_split", split)
     rng = np.random.default_rng(31)
     xw = inputs.blob_image(h, w, c, 1003)
     beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
@@ -63,11 +67,13 @@ def test_tc_blur_stage_fp16(c, h, w):
     assert rel(y, ref) < TOL_BF16, rel(y, ref)
 
 
-def test_tc_blur_stage_bf16_rounding_points():
-    """BF16 operands: the kernel must round exactly beta and H to BF16 and the staged
-    x_w window to FP16 (checked against the oracle with those three tensors rounded),
-    everything else FP32."""
+@pytest.mark.parametrize("split", [1, 0])
+def test_tc_blur_stage_bf16_rounding_points(split):
+    """BF16 operands: each gather kernel must round exactly beta and H to BF16 and the
+    staged x_w window to FP16 (checked against the oracle with those three tensors
+    rounded), everything else FP32."""
     sim = _sim("bf16")
+    sim.set_option("gather_split", split)
     rng = np.random.default_rng(32)
     h, w = 48, 160
     xw = inputs.blob_image(h, w, 3, 1004)
