@@ -242,9 +242,10 @@ p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
  *       operand layout (224 B per pixel of scratch) and a blur-only
  *       tensor-core kernel with four accumulating warps per TMEM lane
  *       quadrant reads it back.
- *       Same rounding points (beta and H in 16 bits, x staged in FP16, FP32
- *       accumulation); results differ from the fused kernel only in the order
- *       of FP32 summation. */
+ *       Rounding points of the fused kernel (beta and H in 16 bits, x staged
+ *       in FP16, FP32 accumulation) plus one: G = beta H is rounded to FP16
+ *       before the tap products (FP16 x FP16, exact in FP32), at most 2^-11
+ *       relative per tap product. */
 typedef enum {
     P2S_OPT_SCATTER_SEGMENT_ROWS = 1,
     P2S_OPT_GRAPHS = 2,

@@ -13,9 +13,10 @@
 //             TMEM (the A operand), then everyone accumulates;
 //   MMA       G = beta H chunk by chunk (N = 96: 3 tap columns x 32 tap rows,
 //             then N = 48 for the last tap row), two TMEM buffers;
-//   gather    y_c[q] += G[q, t] x_c[q - o(t)], x staged as FP16 RGB, FP32
-//             accumulation; the four groups' partial sums are added through
-//             shared memory and written.
+//   gather    y_c[q] += G[q, t] x_c[q - o(t)], x staged as FP16 RGB and G
+//             rounded to FP16, so each product is one fma.rn.f32.f16 (FP16
+//             operands, FP32 accumulation, no conversion of x); the four
+//             groups' partial sums are added through shared memory and written.
 // Every wait is bounded.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -112,14 +113,6 @@ __device__ __forceinline__ uint2 encode_px(float r, float g, float b) {
 }
 
 template <int C>
-__device__ __forceinline__ void decode_px(uint32_t rg_w, uint32_t b_w, float &r, float &g, float &b) {
-    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&rg_w));
-    r = rg.x;
-    g = (C == 3) ? rg.y : 0.f;
-    b = (C == 3) ? __low2float(*reinterpret_cast<const __half2 *>(&b_w)) : 0.f;
-}
-
-template <int C>
 __device__ __forceinline__ void accumulate_pair(const Params &p, const uint4 *xp, uint32_t lane_base, int col, int rp,
                                                 int grp, uint32_t bar0, uint32_t &uses, bool &ok, const Ctl &ctl,
                                                 int lane, float (&acc)[2][3]) {
@@ -145,26 +138,28 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint4 *xp
                 ptx::tmem_ld8(c0, g0);
                 ptx::tmem_ld8(c0 + kMainN, g1);
                 const int txx = 3 * c + u3;
-                float wr[NW + 1], wg[NW + 1], wb[NW + 1];
+                uint4 v[(NW + 1) / 2];  // window rows 2 k, 2 k + 1: (R, G), (B, 0) of each
 #pragma unroll
-                for (int k = 0; k < (NW + 1) / 2; ++k) {
-                    const uint4 v = xp[xw0 + k * kTC - txx];
-                    decode_px<C>(v.x, v.y, wr[2 * k], wg[2 * k], wb[2 * k]);
-                    decode_px<C>(v.z, v.w, wr[2 * k + 1], wg[2 * k + 1], wb[2 * k + 1]);
-                }
+                for (int k = 0; k < (NW + 1) / 2; ++k) v[k] = xp[xw0 + k * kTC - txx];
                 ptx::tmem_wait_ld_dep(g0);
                 ptx::tmem_wait_ld_dep(g1);
 #pragma unroll
                 for (int t = 0; t < NT; ++t) {
-                    const float a = __uint_as_float(g0[t]), bb = __uint_as_float(g1[t]);
-                    if (C == 3) {  // (R, G) as one packed FMA per output row
-                        tcc::fma2_bcast(a, wr[NT - 1 - t], wg[NT - 1 - t], acc[0][0], acc[0][1]);
-                        tcc::fma2_bcast(bb, wr[NT - t], wg[NT - t], acc[1][0], acc[1][1]);
-                        acc[0][2] = fmaf(a, wb[NT - 1 - t], acc[0][2]);
-                        acc[1][2] = fmaf(bb, wb[NT - t], acc[1][2]);
+                    // G of both output rows as one FP16 pair; window rows 7 - t (row 0), 8 - t (row 1)
+                    const uint32_t gp = tcc::pack_f16x2(__uint_as_float(g0[t]), __uint_as_float(g1[t]));
+                    const int w0 = NT - 1 - t, w1 = NT - t;
+                    const uint32_t rg0 = (w0 & 1) ? v[w0 >> 1].z : v[w0 >> 1].x;
+                    const uint32_t b0 = (w0 & 1) ? v[w0 >> 1].w : v[w0 >> 1].y;
+                    const uint32_t rg1 = (w1 & 1) ? v[w1 >> 1].z : v[w1 >> 1].x;
+                    const uint32_t b1 = (w1 & 1) ? v[w1 >> 1].w : v[w1 >> 1].y;
+                    if (C == 3) {
+                        tcc::fma_mix_x2<false>(rg0, gp, acc[0][0], acc[0][1]);
+                        tcc::fma_mix_x2<true>(rg1, gp, acc[1][0], acc[1][1]);
+                        tcc::fma_mix_x1<false>(b0, gp, acc[0][2]);
+                        tcc::fma_mix_x1<true>(b1, gp, acc[1][2]);
                     } else {
-                        acc[0][0] = fmaf(a, wr[NT - 1 - t], acc[0][0]);
-                        acc[1][0] = fmaf(bb, wr[NT - t], acc[1][0]);
+                        tcc::fma_mix_x1<false>(rg0, gp, acc[0][0]);
+                        tcc::fma_mix_x1<true>(rg1, gp, acc[1][0]);
                     }
                 }
             }
@@ -182,18 +177,16 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint4 *xp
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
                 if (q < nq) {
-                    const float a = __uint_as_float(g0[q]), b2 = __uint_as_float(g1[q]);
+                    const uint32_t gp = tcc::pack_f16x2(__uint_as_float(g0[q]), __uint_as_float(g1[q]));
                     const uint2 v0 = xh[xr0 - 2 * q], v1 = xh[xr1 - 2 * q];
-                    float r0, gg0, b0, r1, gg1, b1;
-                    decode_px<C>(v0.x, v0.y, r0, gg0, b0);
-                    decode_px<C>(v1.x, v1.y, r1, gg1, b1);
-                    acc[0][0] = fmaf(a, r0, acc[0][0]);
-                    acc[1][0] = fmaf(b2, r1, acc[1][0]);
                     if (C == 3) {
-                        acc[0][1] = fmaf(a, gg0, acc[0][1]);
-                        acc[0][2] = fmaf(a, b0, acc[0][2]);
-                        acc[1][1] = fmaf(b2, gg1, acc[1][1]);
-                        acc[1][2] = fmaf(b2, b1, acc[1][2]);
+                        tcc::fma_mix_x2<false>(v0.x, gp, acc[0][0], acc[0][1]);
+                        tcc::fma_mix_x2<true>(v1.x, gp, acc[1][0], acc[1][1]);
+                        tcc::fma_mix_x1<false>(v0.y, gp, acc[0][2]);
+                        tcc::fma_mix_x1<true>(v1.y, gp, acc[1][2]);
+                    } else {
+                        tcc::fma_mix_x1<false>(v0.x, gp, acc[0][0]);
+                        tcc::fma_mix_x1<true>(v1.x, gp, acc[1][0]);
                     }
                 }
             }

@@ -48,6 +48,42 @@ __device__ __forceinline__ uint32_t pack2_relu(float a, float b, int fmt) {
     return r;
 }
 
+// g0, g1 rounded to FP16 into one word: g0 in the low half, g1 in the high
+__device__ __forceinline__ uint32_t pack_f16x2(float g0, float g1) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(g1), "f"(g0));
+    return r;
+}
+
+// c0 += lo(x) * g, c1 += hi(x) * g with FP16 operands (x a word of two FP16
+// values, g the low or high half of `gw`) and FP32 accumulation.  The product
+// of two FP16 values is exact in FP32, so each is rounded once, exactly like an
+// fmaf of the widened operands.
+template <bool GHI>
+__device__ __forceinline__ void fma_mix_x2(uint32_t x, uint32_t gw, float &c0, float &c1) {
+    if (GHI)
+        asm("{\n.reg .b16 xl, xh, gl, gh;\nmov.b32 {xl, xh}, %2;\nmov.b32 {gl, gh}, %3;\n"
+            "fma.rn.f32.f16 %0, xl, gh, %0;\nfma.rn.f32.f16 %1, xh, gh, %1;\n}\n"
+            : "+f"(c0), "+f"(c1) : "r"(x), "r"(gw));
+    else
+        asm("{\n.reg .b16 xl, xh, gl, gh;\nmov.b32 {xl, xh}, %2;\nmov.b32 {gl, gh}, %3;\n"
+            "fma.rn.f32.f16 %0, xl, gl, %0;\nfma.rn.f32.f16 %1, xh, gl, %1;\n}\n"
+            : "+f"(c0), "+f"(c1) : "r"(x), "r"(gw));
+}
+
+// c += lo(x) * g, as fma_mix_x2 for one value
+template <bool GHI>
+__device__ __forceinline__ void fma_mix_x1(uint32_t x, uint32_t gw, float &c) {
+    if (GHI)
+        asm("{\n.reg .b16 xl, xh, gl, gh;\nmov.b32 {xl, xh}, %1;\nmov.b32 {gl, gh}, %2;\n"
+            "fma.rn.f32.f16 %0, xl, gh, %0;\n}\n"
+            : "+f"(c) : "r"(x), "r"(gw));
+    else
+        asm("{\n.reg .b16 xl, xh, gl, gh;\nmov.b32 {xl, xh}, %1;\nmov.b32 {gl, gh}, %2;\n"
+            "fma.rn.f32.f16 %0, xl, gl, %0;\n}\n"
+            : "+f"(c) : "r"(x), "r"(gw));
+}
+
 struct Ctl {
     volatile int *abort;
     int *status;

@@ -20,9 +20,11 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-# fused vs split gather: same rounding points, different FP32 summation order; an
-# order change can move a beta entry to the neighbouring 16-bit value
-SPLIT_VS_FUSED = 5e-5
+# fused vs split gather: the split kernel rounds each G[q, t] to FP16 before the
+# tap products (FP16 x FP16 products, FP32 sums), the fused one keeps G in FP32;
+# that is at most 2^-11 relative per tap product (measured 1.9e-4 relative L2 on
+# zero-mean test images, where the sum of |G x| exceeds |y|)
+SPLIT_VS_FUSED = 1e-3
 
 
 def _sim(prec="fp16", form="gather", graphs=False):
@@ -132,9 +134,8 @@ def test_autotune_picks_a_candidate_and_keeps_results(form):
     assert sim.get_option(r["option"]) == r["best"]
     after = sim.simulate(xs, [2.0, 4.0], [3, 4])
     sim.check()
-    # fused and split gather kernels share every rounding point but not the order of
-    # the FP32 sums, so a few beta entries round to the neighbouring FP16 value
-    # (2^-11 relative); each side stays within 2.5e-4 of the FP64 oracle
+    # fused and split gather kernels differ by the FP16 rounding of G in the split
+    # one; each side stays within the 16-bit bound of the FP64 oracle
     tol = SPLIT_VS_FUSED if form == "gather" else 1e-6
     for u, v in zip(before, after):
         assert rel(v.cpu().numpy(), u.cpu().numpy()) < tol
@@ -161,10 +162,10 @@ def test_blur_then_warp_order(prec, form):
 
 @pytest.mark.parametrize("c", [3, 1])
 def test_split_gather_matches_oracle_and_fused(c):
-    """Network kernel, then the blur-only tensor-core gather (three accumulating warps per
-    lane quadrant): same rounding points as the fused kernel, so within FP32 summation
-    order of it, and within the 16-bit bound of the oracle.  Sizes span several tiles,
-    a ragged column tail and an odd last row pair."""
+    """Network kernel, then the blur-only tensor-core gather (four accumulating warps per
+    lane quadrant): the fused kernel's rounding points plus G rounded to FP16, so within
+    that rounding of it, and within the 16-bit bound of the oracle.  Sizes span several
+    tiles, a ragged column tail and an odd last row pair."""
     shapes = [(97, 300), (33, 129), (1, 1), (64, 128)]
     xs = _frames(shapes, c=c, first=2400)
     dr, seeds = [1.5, 3.0, 2.0, 5.0], [71, 72, 73, 74]

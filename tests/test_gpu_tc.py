@@ -67,11 +67,34 @@ def test_tc_blur_stage_fp16(c, h, w, split):
     assert rel(y, ref) < TOL_BF16, rel(y, ref)
 
 
+def _shift(src, dy, dx):
+    """out[i, j] = src[i - dy, j - dx], zero outside the frame."""
+    h, w = src.shape[:2]
+    out = np.zeros_like(src)
+    ys, ye, xs, xe = max(0, -dy), min(h, h - dy), max(0, -dx), min(w, w - dx)
+    if ys < ye and xs < xe:
+        out[ys + dy : ye + dy, xs + dx : xe + dx] = src[ys:ye, xs:xe]
+    return out
+
+
+def _gather_rounded_g(x, beta, Hb, th, tw, g_round):
+    """Eq. 5 gather with every G[q, t] = sum_k beta[q, k] H[k, t] passed through g_round
+    before the tap products (FP64 otherwise): the split kernel's extra rounding point."""
+    h, w, _ = x.shape
+    G = (beta.reshape(h * w, -1).astype(np.float64) @ Hb.astype(np.float64)).reshape(h, w, -1)
+    G = g_round(G)
+    y = np.zeros(x.shape, dtype=np.float64)
+    for i, (dy, dx) in enumerate(oracle.blur.tap_offsets(th, tw)):
+        y += G[:, :, i : i + 1] * _shift(x, dy, dx)
+    return y
+
+
 @pytest.mark.parametrize("split", [1, 0])
 def test_tc_blur_stage_bf16_rounding_points(split):
     """BF16 operands: each gather kernel must round exactly beta and H to BF16 and the
     staged x_w window to FP16 (checked against the oracle with those three tensors
-    rounded), everything else FP32."""
+    rounded), the split kernel also G to FP16 before the tap products; everything else
+    FP32."""
     sim = _sim("bf16")
     sim.set_option("gather_split", split)
     rng = np.random.default_rng(32)
@@ -80,7 +103,12 @@ def test_tc_blur_stage_bf16_rounding_points(split):
     beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
     y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
     x16 = xw.astype(np.float16).astype(np.float64)  # round-to-nearest-even, as the kernel stages it
-    emu = oracle.blur.gather(x16, bf16(beta), bf16(cfg2()["H"]), 33, 33)
+    bb, hb = bf16(beta), bf16(cfg2()["H"])
+    emu = oracle.blur.gather(x16, bb, hb, 33, 33)
+    if split:
+        # the emulation without its rounding is the oracle's gather itself
+        assert rel(_gather_rounded_g(x16, bb, hb, 33, 33, lambda g: g), emu) < 1e-12
+        emu = _gather_rounded_g(x16, bb, hb, 33, 33, lambda g: g.astype(np.float16).astype(np.float64))
     assert rel(y, emu) < 2e-5, rel(y, emu)
 
 
