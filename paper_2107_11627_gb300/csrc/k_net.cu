@@ -66,6 +66,39 @@ enum Bar { kW = 0, kSlotBar0 = 1, kDone = 1 + 6 * kMaxSlots, kNBar = kDone + 1 }
 __host__ __device__ constexpr int barA(int s, int L) { return kSlotBar0 + 6 * s + 2 * L; }      // operand L ready
 __host__ __device__ constexpr int barD(int s, int L) { return kSlotBar0 + 6 * s + 2 * L + 1; }  // D of layer L done
 
+// A unit's place in the batch and the anchors it interpolates from: rows ay
+// (a) and ay + 1 (b) of frame f's anchor grid, columns ax0 .. ax0 + nax - 1.
+struct UnitGeom {
+    int f, row, c0, ax0, nax;
+    float fy;
+    const float *a, *b;
+};
+
+__device__ __forceinline__ UnitGeom unit_geom(const Params &p, int u, int per_frame) {
+    UnitGeom g;
+    g.f = u / per_frame;
+    const int rem = u - g.f * per_frame;
+    const int tcol = rem / p.H;
+    g.row = rem - tcol * p.H;
+    g.c0 = tcol * kTile;
+    const int ay = g.row / p.s;
+    g.fy = (float)(g.row - ay * p.s) * p.inv_s;
+    g.ax0 = min(g.c0, p.W - 1) / p.s;
+    g.nax = min(min(g.c0 + kTile - 1, p.W - 1) / p.s + 2, p.Aw) - g.ax0;
+    g.a = p.alpha + ((size_t)g.f * p.Ah * p.Aw + (size_t)ay * p.Aw + g.ax0) * kAlphaStride;
+    g.b = g.a + (size_t)p.Aw * kAlphaStride;
+    return g;
+}
+
+// element e2 of an interpolated anchor row (anchor e2 / 33, mode 4 + e2 % 33)
+// as an offset from the row's first anchor
+__device__ __forceinline__ int anchor_off(int e2) {
+    const int ax = e2 / kHiModes, k = e2 - ax * kHiModes;
+    return ax * kAlphaStride + k + 3;
+}
+
+constexpr int kPre = 5;  // anchor-row elements per thread loaded one unit ahead (covers 18 anchors)
+
 template <int FMT>  // operand type: 0 FP16, 1 BF16
 __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant__ Params p) {
     extern __shared__ uint8_t smem_raw[];
@@ -149,32 +182,44 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
         uint8_t *abuf = sm + p.offA + slot * kABytes;
         float *arow = (float *)(sm + p.offRow + slot * p.rowBytes);
         const int per_frame = p.H * p.tiles_x;
+        // the two anchor rows of the slot's next unit, first kPre elements per thread,
+        // loaded while the current unit waits for its layer-1 result
+        float pa[kPre], pb[kPre];
+        if (slot < n_local) {
+            const UnitGeom g = unit_geom(p, u_base + slot, per_frame);
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                const int e2 = tid + 128 * q;
+                if (e2 < g.nax * kHiModes) {
+                    const int off = anchor_off(e2);
+                    pa[q] = __ldg(g.a + off);
+                    pb[q] = __ldg(g.b + off);
+                }
+            }
+        }
         for (int i = slot; i < n_local; i += NS) {
             const uint32_t ph = (uint32_t)(i / NS) & 1u;
             const int u = u_base + i;
-            const int f = u / per_frame;
-            const int rem = u - f * per_frame;
-            const int tcol = rem / p.H;
-            const int row = rem - tcol * p.H;
-            const int c0 = tcol * kTile;
+            const UnitGeom g = unit_geom(p, u, per_frame);
+            const int f = g.f, row = g.row, c0 = g.c0;
             const int col = c0 + m;
             bool ok = true;
             // ---- layer-1 operand: alpha_4..36 at (row, col), bilinear from the anchors.
             //      The slot first interpolates the two anchor rows at this image row
             //      (shared by all 128 pixels), then each pixel interpolates along x. ----
             {
-                const int ay = row / p.s;
-                const float fy = (float)(row - ay * p.s) * p.inv_s;
-                const int ax0 = min(c0, p.W - 1) / p.s;
-                const int nax = min(min(c0 + kTile - 1, p.W - 1) / p.s + 2, p.Aw) - ax0;
-                const float *a = p.alpha + ((size_t)f * p.Ah * p.Aw + (size_t)ay * p.Aw + ax0) * kAlphaStride;
-                const float *b = a + (size_t)p.Aw * kAlphaStride;
+                const float fy = g.fy;
+                const int ax0 = g.ax0, nax = g.nax;
                 // every pixel has read the previous unit's anchor row
                 ptx::named_bar(1 + slot, 128);
-                for (int e2 = tid; e2 < nax * kHiModes; e2 += 128) {
-                    const int ax = e2 / kHiModes, k = e2 - ax * kHiModes;
-                    const int off = ax * kAlphaStride + k + 3;
-                    arow[e2] = (1.0f - fy) * __ldg(a + off) + fy * __ldg(b + off);
+#pragma unroll
+                for (int q = 0; q < kPre; ++q) {
+                    const int e2 = tid + 128 * q;
+                    if (e2 < nax * kHiModes) arow[e2] = (1.0f - fy) * pa[q] + fy * pb[q];
+                }
+                for (int e2 = tid + 128 * kPre; e2 < nax * kHiModes; e2 += 128) {
+                    const int off = anchor_off(e2);
+                    arow[e2] = (1.0f - fy) * __ldg(g.a + off) + fy * __ldg(g.b + off);
                 }
                 ptx::named_bar(1 + slot, 128);
                 const int gj = min(col, p.W - 1);
@@ -201,6 +246,18 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                 ptx::fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(BAR(barA(slot, 0)));
+            }
+            if (i + NS < n_local) {
+                const UnitGeom gn = unit_geom(p, u + NS, per_frame);
+#pragma unroll
+                for (int q = 0; q < kPre; ++q) {
+                    const int e2 = tid + 128 * q;
+                    if (e2 < gn.nax * kHiModes) {
+                        const int off = anchor_off(e2);
+                        pa[q] = __ldg(gn.a + off);
+                        pb[q] = __ldg(gn.b + off);
+                    }
+                }
             }
             // ---- layers 1, 2: D -> bias, ReLU -> packed activations (the next A, same buffer) ----
 #pragma unroll 1
