@@ -36,8 +36,8 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per 512x512 RGB frame of each kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
 # 8-frame launch under ncu, divided by 8: the traffic is proportional to the frames, 16-bit beta and
 # x_w exceeding L2 already at 8 frames); valid for the kernels as measured, see profiles/
-DRAM_BYTES_PER_FRAME = {"blur_tc_scatter": (505461760 + 20555520) / 8, "blur_tc_gather16": (495870208 + 20078592) / 8,
-                        "net_tc": (5701632 + 404880896) / 8}
+DRAM_BYTES_PER_FRAME = {"blur_tc_scatter": (505461760 + 20555520) / 8, "blur_tc_gather16": (495983360 + 20459520) / 8,
+                        "net_tc": (5736960 + 405038848) / 8}
 
 
 def workload_name(precision: str, form: str) -> str:
