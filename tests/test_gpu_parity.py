@@ -37,8 +37,9 @@ def test_noise(seed, mode, fh, fw):
     assert np.max(np.abs(z - ref)) < 2e-6
 
 
+# (128, 128, 1): 129 x 129 anchors on a 256 x 256 torus, several CTAs per field in both passes
 @pytest.mark.parametrize("h,w,s,ell", [(64, 64, 8, (16.0,)), (64, 64, 1, (16.0,)), (256, 256, 8, (16.0,)),
-                                       (37, 53, 4, (6.0,)), (1, 1, 8, (16.0,)),
+                                       (37, 53, 4, (6.0,)), (1, 1, 8, (16.0,)), (128, 128, 1, (16.0,)),
                                        (120, 72, 8, (24.0, 20.0, 16.0, 12.0, 10.0, 8.0, 6.0))])
 def test_fields(h, w, s, ell):
     sim = _sim(cfg1(), s=s, ell=ell)
