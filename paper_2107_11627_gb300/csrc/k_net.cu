@@ -1,10 +1,11 @@
 // The P2S network (Sec. 3.3) on the tensor cores as its own persistent
-// kernel, writing beta in the 16-bit operand layout of the scatter blur.
+// kernel, writing beta in the 16-bit operand layout that the blur-only
+// tensor-core kernels (gather and scatter) read.
 //
 // Work unit: 128 consecutive pixels of one image row (one TMEM lane each).
-// Per unit: alpha_4..36 bilinear from the anchors (Sec. 3.4) -> layer 1
-// (A from shared memory) -> ReLU -> layer 2 (A from TMEM, in place) -> ReLU
-// -> layer 3 -> beta, rounded to the operand type and stored as
+// Per unit: alpha_4..36 bilinear from the anchors (Sec. 3.4) -> layer 1 ->
+// ReLU -> layer 2 -> ReLU -> layer 3 (every A operand from shared memory) ->
+// beta, rounded to the operand type and stored as
 //     beta16[frame][row][g][col][8],  g = k / 8 (14 groups, K padded to 112),
 // i.e. one 16-byte run of 8 consecutive k per (pixel, group).  The last
 // layer's bias is left out; with `ones` set, entries k = K, K + 1 hold 1.0
