@@ -245,7 +245,11 @@ p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
  *       Rounding points of the fused kernel (beta and H in 16 bits, x staged
  *       in FP16, FP32 accumulation) plus one: G = beta H is rounded to FP16
  *       before the tap products (FP16 x FP16, exact in FP32), at most 2^-11
- *       relative per tap product. */
+ *       relative per tap product.  A G beyond the FP16 range (|G| > 65504)
+ *       would overflow; PSF weights of the model are orders of magnitude
+ *       smaller (the PSF taps sum to about 1), so this needs beta far outside
+ *       anything the network produces, e.g. hand-made beta given to
+ *       p2s_stage_blur. */
 typedef enum {
     P2S_OPT_SCATTER_SEGMENT_ROWS = 1,
     P2S_OPT_GRAPHS = 2,
