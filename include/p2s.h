@@ -44,7 +44,7 @@ typedef enum {
     P2S_ECUDA = 3,        /* a CUDA runtime call failed                        */
     P2S_ETIMEOUT = 4,     /* a bounded device wait gave up (status word set)   */
     P2S_EBUSY = 5,        /* serving queue or HBM budget full; retry later     */
-    P2S_EUNSUPPORTED = 6  /* valid request this build or device cannot serve   */
+    P2S_EUNSUPPORTED = 6  /* valid request the library or device cannot serve */
 } p2s_status;
 
 /* Arithmetic of the network and the basis contraction.  Fields and warp are
