@@ -345,7 +345,9 @@ p2s_status p2s_profile_read(p2s_ctx *ctx, p2s_kernel_stat *stats, int max_stats,
  * call time, e.g. code held to a fixed, pre-reserved memory budget or a host
  * thread that must stay out of the CUDA allocator).  Same arguments, layout
  * and result as p2s_stage_mlp.  It allocates nothing: the network's weight
- * image is assembled in a 192 KiB array the library holds in device memory
+ * image is assembled in a 163 KiB array (41,728 floats: the largest image
+ * the plain network kernel can stage in its 227 KiB of shared memory beside
+ * its 64 KiB of activation buffers) that the library holds in device memory
  * on every GPU that loads it, for the life of the process.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make that first call
@@ -355,8 +357,9 @@ p2s_status p2s_profile_read(p2s_ctx *ctx, p2s_kernel_stat *stats, int max_stats,
  *     streams, or concurrent host threads) race; serialise them.
  *   - Errors: EUNSUPPORTED for non-FP32 contexts or networks the plain path
  *     does not build; EINVAL if the weight image (weights plus biases, each
- *     bias block padded to 4 floats) exceeds 48 Ki floats, or if the current
- *     device is not the context's. */
+ *     bias block padded to 4 floats) exceeds 41,728 floats, or if the
+ *     current device is not the context's.  p2s_profile records the call as
+ *     "mlp_fp32". */
 p2s_status p2s_stage_mlp_noalloc(p2s_ctx *ctx, int H, int W, const float *alpha, float *beta, void *stream);
 
 /* ---- host-side building blocks ----------------------------------------- */

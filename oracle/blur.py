@@ -12,7 +12,9 @@ With G[p, t] = sum_k beta[p, k] H[k, t] and tap offset o(t) = (ty - th//2, tx - 
   gather   y_c[q]        += G[q, t] x_c[q - o(t)]
 For constant beta both equal one invariant convolution with sum_k beta_k h_k.
 
-exact() is Eq. 3 itself: every pixel spreads its light with its own PSF.
+exact() is Eq. 3 itself: every pixel spreads its light with its own PSF;
+exact_gather() is its row form, every output pixel weighting its
+neighbourhood with its own PSF (what Eq. 5 approximates).
 
 Pins (tests/test_oracle_blur.py): constant beta against scipy.signal's
 convolution, a single basis vector, a delta image, the adjoint identity
@@ -82,4 +84,16 @@ def exact(xw: np.ndarray, psfs: np.ndarray) -> np.ndarray:
     for ty in range(th):
         for tx in range(tw):
             _shift_add(y, psfs[:, :, ty, tx][:, :, None] * xd, ty - th // 2, tx - tw // 2)
+    return y
+
+
+def exact_gather(xw: np.ndarray, psfs: np.ndarray) -> np.ndarray:
+    """Eq. 3 in row form: y[q] = sum_t psfs[q, t] x[q - o(t)], psfs [H, W, th, tw] per OUTPUT pixel."""
+    h, w, c = xw.shape
+    th, tw = psfs.shape[2:]
+    xd = xw.astype(np.float64)
+    y = np.zeros((h, w, c), dtype=np.float64)
+    for ty in range(th):
+        for tx in range(tw):
+            y += psfs[:, :, ty, tx][:, :, None] * _shifted(xd, ty - th // 2, tx - tw // 2)
     return y

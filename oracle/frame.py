@@ -76,8 +76,13 @@ def simulate(x: np.ndarray, seed: int, d_over_r0: float, Hb: np.ndarray, layers,
 
 
 def exact_frame(x: np.ndarray, seed: int, d_over_r0: float, p: fields.CorrParams, taps: tuple[int, int],
-                kap: float | None = None, n_pupil: int = 32, n_fft: int = 64, L: np.ndarray | None = None):
-    """Eq. 3 on a small frame: every pixel's PSF formed by Eq. 2, no basis, no network."""
+                kap: float | None = None, n_pupil: int = 32, n_fft: int = 64, L: np.ndarray | None = None,
+                field_method: str = "fft", form: str = "scatter"):
+    """Eq. 3 on a small frame: every pixel's PSF formed by Eq. 2, no basis, no network.
+
+    Same fields and warp as simulate() for the same arguments.  Returns (x_w, per-pixel PSFs
+    [H, W, th, tw], y); form "scatter" spreads each source pixel's light with its own PSF,
+    "gather" weights each output pixel's neighbourhood with that output pixel's PSF."""
     h, w = x.shape[:2]
     if L is None:
         L = noll.cholesky_lower(noll.noll_cov(36))
@@ -87,7 +92,8 @@ def exact_frame(x: np.ndarray, seed: int, d_over_r0: float, p: fields.CorrParams
     ap = fields.alpha_pixels(aa, h, w, p.anchor_spacing)
     xw = warp.warp(x, ap, kap)
     hp = psf.psf_taps(ap[..., 2:], taps[0], taps[1], n_pupil, n_fft)
-    return xw, hp, blur.exact(xw, hp)
+    fn = blur.exact if form == "scatter" else blur.exact_gather
+    return xw, hp, fn(xw, hp)
 
 
 def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:

@@ -8,6 +8,10 @@ namespace {
 
 constexpr int kMlpThreads = 64;  // pixels per network block
 constexpr int kMaxWidth = 128;
+// Shared memory of the plain network kernel: the weight image plus two activation
+// buffers [kMaxWidth][kMlpThreads]; the image is limited by what is left of 227 KiB.
+constexpr size_t kMlpActBytes = 2ull * kMaxWidth * kMlpThreads * 4;
+constexpr size_t kMlpSmemLimit = 227 * 1024;
 
 struct MlpLayers {
     int n;
@@ -249,33 +253,38 @@ p2s_status launch_blur_c(int H, int W, int K, int th, int tw, int n, const BlurP
 
 }  // namespace
 
-p2s_status launch_mlp_simt(const p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, float *beta,
-                           cudaStream_t st) {
-    if (n <= 0) return P2S_OK;
+// Weight image layout of the plain network kernel: per layer W^T [in][out] then the
+// bias padded to 4 floats.  Returns the image size in floats and the shared memory
+// the kernel needs (the image plus two activation buffers).
+static p2s_status mlp_simt_layout(const p2s_ctx *ctx, MlpLayers *lay, int *floats, size_t *smem) {
     if (ctx->n_layers > 4) {
         set_error("plain network path supports at most 4 layers");
         return P2S_EUNSUPPORTED;
     }
-    MlpLayers lay;
-    lay.n = ctx->n_layers;
+    lay->n = ctx->n_layers;
     int off = 0;
-    for (int l = 0; l < lay.n; ++l) {
-        lay.in[l] = ctx->dims[l];
-        lay.out[l] = ctx->dims[l + 1];
-        lay.w_off[l] = off;
-        off += lay.in[l] * lay.out[l];
-        lay.b_off[l] = off;
-        off += (lay.out[l] + 3) & ~3;
-        lay.relu[l] = l + 1 < lay.n;
+    for (int l = 0; l < lay->n; ++l) {
+        lay->in[l] = ctx->dims[l];
+        lay->out[l] = ctx->dims[l + 1];
+        lay->w_off[l] = off;
+        off += lay->in[l] * lay->out[l];
+        lay->b_off[l] = off;
+        off += (lay->out[l] + 3) & ~3;
+        lay->relu[l] = l + 1 < lay->n;
     }
-    const size_t smem = (size_t)off * 4 + 2ull * kMaxWidth * kMlpThreads * 4;
-    if (smem > 227 * 1024) {
-        set_error("network too large for the plain path (%zu bytes of shared memory)", smem);
+    *floats = off;
+    *smem = (size_t)off * 4 + kMlpActBytes;
+    if (*smem > kMlpSmemLimit) {
+        set_error("network too large for the plain path (%zu bytes of shared memory)", *smem);
         return P2S_EUNSUPPORTED;
     }
-    // The weight image is assembled once per call from the per-layer device copies.
-    float *wimg = nullptr;
-    P2S_CUDA(cudaMallocAsync((void **)&wimg, (size_t)off * 4, st));
+    return P2S_OK;
+}
+
+// Fills the weight image `wimg` (device, `floats` long) from the context's per-layer
+// copies and launches the kernel over n frames, all on stream `st`.
+static p2s_status mlp_simt_run(const p2s_ctx *ctx, const MlpLayers &lay, int floats, size_t smem, const FieldGeom &g,
+                               int n, float *wimg, const float *alpha, float *beta, cudaStream_t st) {
     for (int l = 0; l < lay.n; ++l) {
         P2S_CUDA(cudaMemcpyAsync(wimg + lay.w_off[l], ctx->d_Wt32[l], (size_t)lay.in[l] * lay.out[l] * 4,
                                  cudaMemcpyDeviceToDevice, st));
@@ -291,11 +300,26 @@ p2s_status launch_mlp_simt(const p2s_ctx *ctx, const FieldGeom &g, int n, const 
     for (int l = 0; l < lay.n; ++l) macs += (double)lay.in[l] * lay.out[l];
     const double npx = (double)g.H * g.W * n;
     ProfScope pr(ctx, st, "mlp_fp32", 2.0 * macs * npx, npx * ctx->K * 4);
-    mlp_simt_kernel<<<grid, kMlpThreads, smem, st>>>(lay, off, n, g.H, g.W, g.s, 1.0f / g.s, g.Aw, g.Ah * g.Aw, wimg,
-                                                     alpha, beta);
+    mlp_simt_kernel<<<grid, kMlpThreads, smem, st>>>(lay, floats, n, g.H, g.W, g.s, 1.0f / g.s, g.Aw, g.Ah * g.Aw,
+                                                     wimg, alpha, beta);
     P2S_CUDA(cudaGetLastError());
-    cudaFreeAsync(wimg, st);
     return P2S_OK;
+}
+
+p2s_status launch_mlp_simt(const p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, float *beta,
+                           cudaStream_t st) {
+    if (n <= 0) return P2S_OK;
+    MlpLayers lay;
+    int floats = 0;
+    size_t smem = 0;
+    p2s_status rc = mlp_simt_layout(ctx, &lay, &floats, &smem);
+    if (rc != P2S_OK) return rc;
+    // The weight image is assembled once per call from the per-layer device copies.
+    float *wimg = nullptr;
+    P2S_CUDA(cudaMallocAsync((void **)&wimg, (size_t)floats * 4, st));
+    rc = mlp_simt_run(ctx, lay, floats, smem, g, n, wimg, alpha, beta, st);
+    cudaFreeAsync(wimg, st);
+    return rc;
 }
 
 p2s_status launch_blur_simt(const p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw,
@@ -336,7 +360,10 @@ p2s_status launch_blur_simt(const p2s_ctx *ctx, int H, int W, int C, int n, cons
 namespace p2s {
 namespace {
 
-constexpr int kNoAllocWeightFloats = 48 * 1024;  // 192 KiB: weight image limit of the variant
+// Weight image limit of the variant: the largest image the plain network kernel can
+// stage in shared memory, (227 KiB - 64 KiB of activation buffers) / 4 = 41,728 floats
+// (163 KiB).
+constexpr int kNoAllocWeightFloats = (int)((kMlpSmemLimit - kMlpActBytes) / 4);
 static __device__ __align__(256) float g_noalloc_weights[kNoAllocWeightFloats];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -382,31 +409,20 @@ extern "C" p2s_status p2s_stage_mlp_noalloc(p2s_ctx *ctx, int H, int W, const fl
     FieldGeom g;
     p2s_status st = geometry(ctx, H, W, &g);
     if (st != P2S_OK) return st;
-    if (ctx->n_layers > 4) {
-        set_error("plain network path supports at most 4 layers");
-        return P2S_EUNSUPPORTED;
-    }
     MlpLayers lay;
-    lay.n = ctx->n_layers;
-    int off = 0;
-    for (int l = 0; l < lay.n; ++l) {
-        lay.in[l] = ctx->dims[l];
-        lay.out[l] = ctx->dims[l + 1];
-        lay.w_off[l] = off;
-        off += lay.in[l] * lay.out[l];
-        lay.b_off[l] = off;
-        off += (lay.out[l] + 3) & ~3;
-        lay.relu[l] = l + 1 < lay.n;
+    int floats = 0;
+    size_t smem = 0;
+    // Size check first: an image beyond the array is the caller's argument error.
+    {
+        int off = 0;
+        for (int l = 0; l < ctx->n_layers; ++l) off += ctx->dims[l] * ctx->dims[l + 1] + ((ctx->dims[l + 1] + 3) & ~3);
+        if (off > kNoAllocWeightFloats) {
+            set_error("network weights need %d floats; the allocation-free scratch holds %d", off,
+                      kNoAllocWeightFloats);
+            return P2S_EINVAL;
+        }
     }
-    if (off > kNoAllocWeightFloats) {
-        set_error("network weights need %d floats; the allocation-free scratch holds %d", off, kNoAllocWeightFloats);
-        return P2S_EINVAL;
-    }
-    const size_t smem = (size_t)off * 4 + 2ull * kMaxWidth * kMlpThreads * 4;
-    if (smem > 227 * 1024) {
-        set_error("network too large for the plain path (%zu bytes of shared memory)", smem);
-        return P2S_EUNSUPPORTED;
-    }
+    if ((st = mlp_simt_layout(ctx, &lay, &floats, &smem)) != P2S_OK) return st;
     int dev = -1;
     P2S_CUDA(cudaGetDevice(&dev));
     if (dev != ctx->device) {
@@ -415,22 +431,7 @@ extern "C" p2s_status p2s_stage_mlp_noalloc(p2s_ctx *ctx, int H, int W, const fl
     }
     float *wimg = nullptr;
     if ((st = noalloc_weights_on(dev, &wimg)) != P2S_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     // The image is rewritten in full by every call; the padding floats after
     // each bias block are never read, so nothing needs clearing.
-    for (int l = 0; l < lay.n; ++l) {
-        P2S_CUDA(cudaMemcpyAsync(wimg + lay.w_off[l], ctx->d_Wt32[l], (size_t)lay.in[l] * lay.out[l] * 4,
-                                 cudaMemcpyDeviceToDevice, s));
-        P2S_CUDA(cudaMemcpyAsync(wimg + lay.b_off[l], ctx->d_b32[l], (size_t)lay.out[l] * 4, cudaMemcpyDeviceToDevice,
-                                 s));
-    }
-    P2S_CUDA(cudaFuncSetAttribute(mlp_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    const long long nblk = ((long long)g.H * g.W + kMlpThreads - 1) / kMlpThreads;
-    const int grid = (int)(nblk < 2LL * sms ? nblk : 2LL * sms);
-    mlp_simt_kernel<<<grid, kMlpThreads, smem, s>>>(lay, off, 1, g.H, g.W, g.s, 1.0f / g.s, g.Aw, g.Ah * g.Aw, wimg,
-                                                    alpha, beta);
-    P2S_CUDA(cudaGetLastError());
-    return P2S_OK;
+    return mlp_simt_run(ctx, lay, floats, smem, g, 1, wimg, alpha, beta, (cudaStream_t)stream);
 }

@@ -30,5 +30,34 @@ def cfg2():
     return dict(H=basis(100, 33, 4000), taps=(33, 33), layers=inputs.mlp_weights([33, 128, 128, 100], 42))
 
 
+# Element-wise bound: every |a - ref| <= MAXABS_FACTOR * tol * max|ref|.  The relative-L2
+# tolerance bounds the rms error; the tail of the element errors of a correct kernel sits a
+# few rms above it, while one wrong tile or border strip shows up as an error of the order
+# of the values themselves, far above this bound.
+MAXABS_FACTOR = 10.0
+
+# (test, what, rel_l2, max_abs, max_abs_bound, tol) of every comparison, printed at the end of
+# the run by conftest.py so that the log's tail carries the figures.
+RECORDS: list = []
+
+
 def rel(a, b):
     return oracle.frame.rel_l2(a, b)
+
+
+def close(a, ref, tol, what=""):
+    """Assert relative L2 < tol and the element-wise bound above; record both figures."""
+    import os
+
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert a.shape == ref.shape, (what, a.shape, ref.shape)
+    r = rel(a, ref)
+    mx = float(np.max(np.abs(a - ref))) if a.size else 0.0
+    bound = MAXABS_FACTOR * tol * (float(np.max(np.abs(ref))) if ref.size else 0.0)
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0].split("::")[-1]
+    RECORDS.append((test, str(what), r, mx, bound, tol))
+    assert np.all(np.isfinite(a)), (what, "non-finite output")
+    assert r < tol, (what, "rel_l2", r, tol)
+    assert mx <= bound, (what, "max_abs", mx, bound)
+    return r, mx

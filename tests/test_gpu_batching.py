@@ -7,7 +7,7 @@ import oracle
 from oracle.fields import CorrParams
 from paper_2107_11627_gb300 import inputs
 
-from gpu_common import TOL_BF16, cfg2, rel
+from gpu_common import TOL_BF16, cfg2, rel, close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,7 +57,7 @@ def test_uneven_batch_matches_oracle_and_is_batch_invariant():
     for i in (0, len(xs) - 1, 3):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form="gather")
-        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_BF16, (i, shapes[i] if i < len(shapes) else None)
+        close(ys[i].cpu().numpy(), ref.y, TOL_BF16, i)
     for i in (1, len(xs) - 1):
         (alone,) = sim.simulate([torch.from_numpy(xs[i]).cuda()], [dr[i]], [seeds[i]])
         assert torch.equal(alone, ys[i])
@@ -80,7 +80,7 @@ def test_graph_mode_matches_plain_launches(form):
             if form == "gather":
                 assert torch.equal(u, v)
             else:  # atomic adds at segment boundaries may differ in summation order
-                assert rel(v.cpu().numpy(), u.cpu().numpy()) < 1e-6
+                close(v.cpu().numpy(), u.cpu().numpy(), 1e-6)
     assert graph.get_option("graph_instantiations") == 1
     assert graph.get_option("graph_updates") == 2
     # a new signature instantiates a second graph
@@ -138,7 +138,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(form):
     # one; each side stays within the 16-bit bound of the FP64 oracle
     tol = SPLIT_VS_FUSED if form == "gather" else 1e-6
     for u, v in zip(before, after):
-        assert rel(v.cpu().numpy(), u.cpu().numpy()) < tol
+        close(v.cpu().numpy(), u.cpu().numpy(), tol)
 
 
 @pytest.mark.parametrize("prec,form", [("fp16", "gather"), ("fp16", "scatter"), ("fp32", "scatter")])
@@ -157,7 +157,7 @@ def test_blur_then_warp_order(prec, form):
     for i in range(2):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form=form, order="blur_warp")
-        assert rel(ys[i].cpu().numpy(), ref.y) < tol, (i, rel(ys[i].cpu().numpy(), ref.y))
+        close(ys[i].cpu().numpy(), ref.y, tol, i)
 
 
 @pytest.mark.parametrize("c", [3, 1])
@@ -180,11 +180,11 @@ def test_split_gather_matches_oracle_and_fused(c):
     fused.check()
     split.check()
     for i in range(len(xs)):
-        assert rel(yb[i].cpu().numpy(), ya[i].cpu().numpy()) < SPLIT_VS_FUSED, (i, shapes[i])
+        close(yb[i].cpu().numpy(), ya[i].cpu().numpy(), SPLIT_VS_FUSED, i)
     for i in (0, 1):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form="gather")
-        assert rel(yb[i].cpu().numpy(), ref.y) < TOL_BF16, (i, rel(yb[i].cpu().numpy(), ref.y))
+        close(yb[i].cpu().numpy(), ref.y, TOL_BF16, i)
     (alone,) = split.simulate([xd[1]], [dr[1]], [seeds[1]])
     split.check()
     assert torch.equal(alone, yb[1])
@@ -207,7 +207,7 @@ def test_split_gather_blur_then_warp_and_graphs():
         ref = oracle.frame.simulate(xs[i].cpu().numpy().astype(np.float64), [5, 6][i], [2.0, 4.0][i], cfg2()["H"],
                                     cfg2()["layers"], CorrParams(8, (16.0,)), (33, 33), form="gather",
                                     order="blur_warp")
-        assert rel(ya[i].cpu().numpy(), ref.y) < TOL_BF16
+        close(ya[i].cpu().numpy(), ref.y, TOL_BF16)
 
 
 def test_host_entry_point_pipelines_chunks_bit_exact():

@@ -7,7 +7,7 @@ import oracle
 from oracle.fields import CorrParams
 from paper_2107_11627_gb300 import inputs
 
-from gpu_common import TOL_BF16, TOL_FIELD, cfg1, cfg2, rel
+from gpu_common import TOL_BF16, TOL_FIELD, cfg1, cfg2, rel, close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,7 +41,7 @@ def test_dense_fields(h, w, s, ell):
     assert np.all(a[..., 0] == 0)
     for i in range(2):
         ref = oracle.fields.alpha_anchors(seeds[i], dr[i], h, w, p, method="dense")
-        assert rel(a[i, ..., 1:], ref) < TOL_FIELD, (i, rel(a[i, ..., 1:], ref))
+        close(a[i, ..., 1:], ref, TOL_FIELD, i)
 
 
 def test_dense_fields_frames_tensor_core():
@@ -54,7 +54,7 @@ def test_dense_fields_frames_tensor_core():
     for i in range(2):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form="gather", field_method="dense")
-        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_BF16, (i, rel(ys[i].cpu().numpy(), ref.y))
+        close(ys[i].cpu().numpy(), ref.y, TOL_BF16, i)
 
 
 def test_dense_fields_too_many_anchors_are_refused():

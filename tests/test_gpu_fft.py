@@ -7,7 +7,7 @@ import oracle
 from oracle.fields import CorrParams
 from paper_2107_11627_gb300 import inputs
 
-from gpu_common import TOL_FP32, cfg2, rel
+from gpu_common import TOL_FP32, cfg2, rel, close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -38,7 +38,7 @@ def test_fft_blur_stage(c, h, w):
     y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda())
     sim.check()
     ref = oracle.blur.scatter(xw.astype(np.float64), beta.astype(np.float64), cfg2()["H"], 33, 33)
-    assert rel(y.cpu().numpy(), ref) < TOL_FP32, rel(y.cpu().numpy(), ref)
+    close(y.cpu().numpy(), ref, TOL_FP32)
 
 
 def test_fft_frames_match_oracle_and_direct_path():
@@ -50,8 +50,8 @@ def test_fft_frames_match_oracle_and_direct_path():
     for i in range(2):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form="scatter")
-        assert rel(fft[i].cpu().numpy(), ref.y) < TOL_FP32
-        assert rel(fft[i].cpu().numpy(), direct[i].cpu().numpy()) < TOL_FP32
+        close(fft[i].cpu().numpy(), ref.y, TOL_FP32)
+        close(fft[i].cpu().numpy(), direct[i].cpu().numpy(), TOL_FP32)
 
 
 def test_fft_needs_fp32():

@@ -8,7 +8,7 @@ import oracle
 from oracle.fields import CorrParams
 from paper_2107_11627_gb300 import inputs
 
-from gpu_common import TOL_FIELD, TOL_FP32, cfg1, cfg2, rel
+from gpu_common import TOL_FIELD, TOL_FP32, cfg1, cfg2, rel, close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -33,7 +33,7 @@ def test_noise(seed, mode, fh, fw):
     sim = _sim(cfg1())
     z = sim.stage_noise(seed, mode, fh, fw).cpu().numpy().astype(np.float64)
     ref = oracle.philox.normals(seed, mode, fh * fw).reshape(fh, fw)
-    assert rel(z, ref) < TOL_FIELD / 4
+    close(z, ref, TOL_FIELD / 4)
     assert np.max(np.abs(z - ref)) < 2e-6
 
 
@@ -51,7 +51,7 @@ def test_fields(h, w, s, ell):
     for i in range(2):
         ref = oracle.fields.alpha_anchors(seeds[i], dr[i], h, w, p)
         assert a.shape[1:3] == ref.shape[:2]
-        assert rel(a[i, ..., 1:], ref) < TOL_FIELD, (i, rel(a[i, ..., 1:], ref))
+        close(a[i, ..., 1:], ref, TOL_FIELD, i)
 
 
 def _alpha_f32(seed, dr, h, w, p):
@@ -71,7 +71,7 @@ def test_warp(h, w, c, s, dr):
     xw = sim.stage_warp(torch.from_numpy(x).cuda(), torch.from_numpy(al).cuda()).cpu().numpy()
     ap = oracle.fields.alpha_pixels(al[..., 1:].astype(np.float64), h, w, s)
     ref = oracle.warp.warp(x.astype(np.float64), ap, oracle.warp.kappa())
-    assert rel(xw, ref) < TOL_FIELD
+    close(xw, ref, TOL_FIELD)
 
 
 @pytest.mark.parametrize("which,h,w", [("cfg1", 64, 64), ("cfg2", 45, 70)])
@@ -83,7 +83,7 @@ def test_mlp(which, h, w):
     beta = sim.stage_mlp(h, w, torch.from_numpy(al).cuda()).cpu().numpy()
     ap = oracle.fields.alpha_pixels(al[..., 1:].astype(np.float64), h, w, 8)
     ref = oracle.mlp.forward(ap[..., 2:], cfg["layers"])
-    assert rel(beta, ref) < TOL_FP32
+    close(beta, ref, TOL_FP32)
 
 
 @pytest.mark.parametrize("form", ["scatter", "gather"])
@@ -97,7 +97,7 @@ def test_blur(form, which, h, w, c):
     y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
     fn = oracle.blur.scatter if form == "scatter" else oracle.blur.gather
     ref = fn(xw.astype(np.float64), beta.astype(np.float64), cfg["H"], *cfg["taps"])
-    assert rel(y, ref) < TOL_FP32
+    close(y, ref, TOL_FP32)
 
 
 @pytest.mark.parametrize("form", ["scatter", "gather"])
@@ -109,7 +109,7 @@ def test_frame_cfg1(form, s):
     (y,) = sim.simulate([torch.from_numpy(x).cuda()], [2.0], [10**6])
     ref = oracle.frame.simulate(x.astype(np.float64), 10**6, 2.0, cfg["H"], cfg["layers"], CorrParams(s, (16.0,)),
                                 cfg["taps"], form=form)
-    assert rel(y.cpu().numpy(), ref.y) < TOL_FP32
+    close(y.cpu().numpy(), ref.y, TOL_FP32)
 
 
 def test_frame_cfg2_batch_and_invariance():
@@ -124,9 +124,9 @@ def test_frame_cfg2_batch_and_invariance():
     for i in range(3):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg["H"], cfg["layers"],
                                     CorrParams(8, (16.0,)), cfg["taps"])
-        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_FP32, i
+        close(ys[i].cpu().numpy(), ref.y, TOL_FP32, i)
         (alone,) = sim.simulate([xt[i]], [dr[i]], [seeds[i]])
-        assert rel(alone.cpu().numpy(), ys[i].cpu().numpy()) < 1e-6
+        close(alone.cpu().numpy(), ys[i].cpu().numpy(), 1e-6)
     assert sim.simulate([], [], []) == []
 
 
@@ -142,7 +142,7 @@ def test_frame_cfg2_full_size_batch():
     for i in (0, 11):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), int(seeds[i]), float(dr[i]), cfg["H"], cfg["layers"],
                                     CorrParams(8, (16.0,)), cfg["taps"])
-        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_FP32, (i, rel(ys[i].cpu().numpy(), ref.y))
+        close(ys[i].cpu().numpy(), ref.y, TOL_FP32, i)
 
 
 def test_host_entry_point_matches_device():
@@ -151,7 +151,7 @@ def test_host_entry_point_matches_device():
     x = inputs.block_image(64, 64, 8, 1, 1000)
     (yd,) = sim.simulate([torch.from_numpy(x).cuda()], [2.0], [10**6])
     (yh,) = sim.simulate_host([x], [2.0], [10**6])
-    assert rel(yh, yd.cpu().numpy()) < 1e-6
+    close(yh, yd.cpu().numpy(), 1e-6)
 
 
 def test_invalid_arguments():

@@ -7,7 +7,7 @@ import oracle
 from oracle.fields import CorrParams
 from paper_2107_11627_gb300 import inputs
 
-from gpu_common import TOL_BF16, cfg2, rel
+from gpu_common import TOL_BF16, cfg2, rel, close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,11 +59,11 @@ def test_results_equal_alone_and_in_the_mix(form):
         if form == "gather":
             assert np.array_equal(a, o)
         else:
-            assert rel(o, a) < 1e-6
+            close(o, a, 1e-6)
     x, dr, sd = reqs[1]
     want = oracle.frame.simulate(x.astype(np.float64), sd, dr, cfg2()["H"], cfg2()["layers"], CorrParams(8, (16.0,)),
                                  (33, 33), form=form)
-    assert rel(outs[1], want.y) < TOL_BF16
+    close(outs[1], want.y, TOL_BF16)
 
 
 def test_admission_holds_the_budget():

@@ -8,7 +8,7 @@ from oracle.fields import CorrParams
 from oracle.precision import bf16
 from paper_2107_11627_gb300 import inputs
 
-from gpu_common import TOL_BF16, cfg2, rel
+from gpu_common import TOL_BF16, cfg2, rel, close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,7 +46,7 @@ def test_tc_network_stage(prec, h, w):
     beta = beta.cpu().numpy()
     ap = oracle.fields.alpha_pixels(al[..., 1:].astype(np.float64), h, w, 8)
     ref = oracle.mlp.forward(ap[..., 2:], cfg2()["layers"])
-    assert rel(beta, ref) < TOL_BF16, rel(beta, ref)
+    close(beta, ref, TOL_BF16)
 
 
 @pytest.mark.parametrize("split", [1, 0])
@@ -64,7 +64,7 @@ def test_tc_blur_stage_fp16(c, h, w, split):
     sim.check()
     y = y.cpu().numpy()
     ref = oracle.blur.gather(xw.astype(np.float64), beta.astype(np.float64), cfg2()["H"], 33, 33)
-    assert rel(y, ref) < TOL_BF16, rel(y, ref)
+    close(y, ref, TOL_BF16)
 
 
 def _shift(src, dy, dx):
@@ -109,7 +109,7 @@ def test_tc_blur_stage_bf16_rounding_points(split):
         # the emulation without its rounding is the oracle's gather itself
         assert rel(_gather_rounded_g(x16, bb, hb, 33, 33, lambda g: g), emu) < 1e-12
         emu = _gather_rounded_g(x16, bb, hb, 33, 33, lambda g: g.astype(np.float16).astype(np.float64))
-    assert rel(y, emu) < 2e-5, rel(y, emu)
+    close(y, emu, 2e-5)
 
 
 @pytest.mark.parametrize("s", [8, 1])
@@ -123,7 +123,7 @@ def test_tc_frames_fp16(s):
     for i in range(3):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(s, (16.0,)), (33, 33), form="gather")
-        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_BF16, (i, rel(ys[i].cpu().numpy(), ref.y))
+        close(ys[i].cpu().numpy(), ref.y, TOL_BF16, i)
 
 
 def test_tc_full_size_frame_fp16():
@@ -133,4 +133,4 @@ def test_tc_full_size_frame_fp16():
     (y,) = sim.simulate([torch.from_numpy(x).cuda()], [3.0], [10**6])
     ref = oracle.frame.simulate(x.astype(np.float64), 10**6, 3.0, cfg2()["H"], cfg2()["layers"],
                                 CorrParams(8, (16.0,)), (33, 33), form="gather")
-    assert rel(y.cpu().numpy(), ref.y) < TOL_BF16
+    close(y.cpu().numpy(), ref.y, TOL_BF16)

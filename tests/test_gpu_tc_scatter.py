@@ -9,7 +9,7 @@ from oracle.fields import CorrParams
 from oracle.precision import bf16
 from paper_2107_11627_gb300 import inputs
 
-from gpu_common import TOL_BF16, cfg2, rel
+from gpu_common import TOL_BF16, cfg2, rel, close
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -66,7 +66,7 @@ def test_network_operand_layout(prec, h, w):
     ap = oracle.fields.alpha_pixels(al[..., 1:].astype(np.float64), h, w, 8)
     ref = oracle.mlp.forward(ap[..., 2:], layers) - layers[-1][1]
     tol = TOL_BF16 if prec == "fp16" else 4e-3
-    assert rel(v[..., :100], ref) < tol, rel(v[..., :100], ref)
+    close(v[..., :100], ref, tol)
     assert np.all(v[..., 100:102] == 1.0)
     assert np.all(v[..., 102:] == 0.0)
 
@@ -82,7 +82,7 @@ def test_blur_stage_fp16(c, h, w):
     sim.check()
     y = y.cpu().numpy()
     ref = oracle.blur.scatter(xw.astype(np.float64), beta.astype(np.float64), cfg2()["H"], 33, 33)
-    assert rel(y, ref) < TOL_BF16, rel(y, ref)
+    close(y, ref, TOL_BF16)
 
 
 @pytest.mark.parametrize("seg", [2, 6, 34, 128])
@@ -97,7 +97,7 @@ def test_blur_stage_segments(seg):
     y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
     sim.check()
     ref = oracle.blur.scatter(xw.astype(np.float64), beta.astype(np.float64), cfg2()["H"], 33, 33)
-    assert rel(y, ref) < TOL_BF16, rel(y, ref)
+    close(y, ref, TOL_BF16)
 
 
 def test_blur_stage_bf16_rounding_points():
@@ -110,7 +110,7 @@ def test_blur_stage_bf16_rounding_points():
     beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
     y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
     emu = oracle.blur.scatter(xw.astype(np.float64), bf16(beta), bf16(cfg2()["H"]), 33, 33)
-    assert rel(y, emu) < 2e-5, rel(y, emu)
+    close(y, emu, 2e-5)
 
 
 @pytest.mark.parametrize("s", [8, 1])
@@ -124,7 +124,7 @@ def test_frames_fp16(s):
     for i in range(3):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(s, (16.0,)), (33, 33), form="scatter")
-        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_BF16, (i, rel(ys[i].cpu().numpy(), ref.y))
+        close(ys[i].cpu().numpy(), ref.y, TOL_BF16, i)
 
 
 def test_full_size_frame_fp16():
@@ -135,7 +135,7 @@ def test_full_size_frame_fp16():
     sim.check()
     ref = oracle.frame.simulate(x.astype(np.float64), 10**6, 3.0, cfg2()["H"], cfg2()["layers"],
                                 CorrParams(8, (16.0,)), (33, 33), form="scatter")
-    assert rel(y.cpu().numpy(), ref.y) < TOL_BF16
+    close(y.cpu().numpy(), ref.y, TOL_BF16)
 
 
 def test_batch_invariance_fp16():
@@ -146,7 +146,7 @@ def test_batch_invariance_fp16():
     ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], [2.0, 3.0, 4.0], [7, 8, 9])
     (alone,) = sim.simulate([torch.from_numpy(xs[2]).cuda()], [4.0], [9])
     sim.check()
-    assert rel(ys[2].cpu().numpy(), alone.cpu().numpy()) < 1e-6
+    close(ys[2].cpu().numpy(), alone.cpu().numpy(), 1e-6)
 
 
 def test_frames_bf16_within_contract():
@@ -161,4 +161,4 @@ def test_frames_bf16_within_contract():
     for i in range(2):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form="scatter")
-        assert rel(ys[i].cpu().numpy(), ref.y) < TOL_BF16, (i, rel(ys[i].cpu().numpy(), ref.y))
+        close(ys[i].cpu().numpy(), ref.y, TOL_BF16, i)
