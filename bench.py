@@ -312,6 +312,8 @@ def main():
     ap.add_argument("--frames", type=int, default=64, help="frames per step (profiling runs only)")
     ap.add_argument("--no-batching", action="store_true", help="skip the uneven-size batching workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
+    ap.add_argument("--gather-split", type=int, default=None,
+                    help="tensor-core gather kernel: 0 fused, 1 or 2 blur-only (default: the library's)")
     args = ap.parse_args()
     N_FRAMES = args.frames
     if args.impl == "reference":
@@ -327,6 +329,8 @@ def main():
     layers = inputs.mlp_weights(DIMS, 42)
     sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,),
                         precision=args.precision, form=args.form)
+    if args.gather_split is not None:
+        sim.set_option("gather_split", args.gather_split)
     share = replica_inputs(rank, N_FRAMES)
     xs_host = inputs.blob_batch(N_FRAMES, HW, HW, CH, share["image_seed"])
     dr = share["d_over_r0"]

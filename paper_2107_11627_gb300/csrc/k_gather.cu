@@ -200,7 +200,9 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint4 *xp
 template <int C>
 __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_constant__ Params p) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned by pointer arithmetic on the __shared__ array, so that the compiler still
+    // knows every access through `sm` is to shared memory (ld/st.shared, not generic)
+    uint8_t *sm = smem_raw + ((1024u - (uint32_t)((uintptr_t)smem_raw & 1023u)) & 1023u);
     const uint32_t sbase = ptx::smem_u32(sm);
     uint4 *xp = (uint4 *)(sm + kOffX);
     float *xchg = (float *)(sm + kOffXchg);

@@ -56,7 +56,7 @@ struct Params {
     int *status;
     int n, H, W, s, Ah, Aw;
     float inv_s;
-    int K, h1p, h2p, n3, ab_fmt, per, ones;
+    int K, h1p, h2p, n3, ab_fmt, per, ones, perm, pitch;
     int tiles_x, tiles_total, per_cta, nslots;
     uint32_t wbytes, offA, offRow, rowBytes, offBias, offBar, offMisc;
     uint32_t item_off[kMaxItems], item_bytes[kMaxItems], item_n[kMaxItems], item_k[kMaxItems], item_soff[kMaxItems];
@@ -103,7 +103,9 @@ constexpr int kPre = 5;  // anchor-row elements per thread loaded one unit ahead
 template <int FMT>  // operand type: 0 FP16, 1 BF16
 __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant__ Params p) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned by pointer arithmetic on the __shared__ array, so that the compiler still
+    // knows every access through `sm` is to shared memory (ld/st.shared, not generic)
+    uint8_t *sm = smem_raw + ((1024u - (uint32_t)((uintptr_t)smem_raw & 1023u)) & 1023u);
     const uint32_t sbase = ptx::smem_u32(sm);
     float *sbias = (float *)(sm + p.offBias);
     uint32_t *tmem_holder = (uint32_t *)(sm + p.offMisc);
@@ -298,7 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
             ok = __all_sync(0xffffffffu, wait_bar(BAR(barD(slot, 2)), ph, ctl, 8) && ok);
             ptx::fence_after();
             const bool store = ok && f < p.n && col < p.W;
-            uint4 *dst = p.beta16 + ((size_t)(f * p.H + row) * kGroups) * p.W + col;
+            const int pos = p.perm ? (col & ~31) + 8 * (col & 3) + ((col & 31) >> 2) : col;
+            uint4 *dst = p.beta16 + ((size_t)(f * p.H + row) * kGroups) * p.pitch + pos;
 #pragma unroll 1
             for (int c32 = 0; ok && c32 < 8 * kGroups; c32 += 32) {  // columns 112..127 are read, unused
                 uint32_t d[32];
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                             w4.y = pack2(v[2], v[3], FMT);
                             w4.z = pack2(v[4], v[5], FMT);
                             w4.w = pack2(v[6], v[7], FMT);
-                            dst[(size_t)g * p.W] = w4;
+                            dst[(size_t)g * p.pitch] = w4;
                         }
                     }
                 }
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
 
 // beta FP32 [n][H][W][K] -> beta16 (no bias fold: entries k >= K are 0)
 __global__ void pack16_kernel(const float *__restrict__ beta, uint4 *__restrict__ out, long long npx, int W, int K,
-                              int fmt) {
+                              int fmt, int perm, int pitch) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (pixel, group)
     if (i >= npx * kGroups) return;
     const long long px = i / kGroups;
@@ -364,14 +367,15 @@ __global__ void pack16_kernel(const float *__restrict__ beta, uint4 *__restrict_
     u.y = pack2(v[2], v[3], fmt);
     u.z = pack2(v[4], v[5], fmt);
     u.w = pack2(v[6], v[7], fmt);
-    out[(rowf * kGroups + g) * W + col] = u;
+    const int pos = perm ? (col & ~31) + 8 * (col & 3) + ((col & 31) >> 2) : col;
+    out[(rowf * kGroups + g) * pitch + pos] = u;
 }
 
 }  // namespace net
 
 using namespace net;
 
-size_t beta16_bytes(int H, int W, int n) { return (size_t)n * H * W * kGroups * 16; }
+size_t beta16_bytes(int H, int W, int n, int perm) { return (size_t)n * H * beta16_pitch(W, perm) * kGroups * 16; }
 
 // Shared-memory layout of the network kernel for a geometry; returns the
 // bytes needed and fills the offsets and the slot count (0 if nothing fits).
@@ -395,7 +399,7 @@ static int net_layout(const p2s_ctx *ctx, int s, int W, Params *p) {
     return (int)(p->offMisc + 16 + 1024);
 }
 
-p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones,
+p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones, int perm,
                         int *status, cudaStream_t st) {
     if (n <= 0) return P2S_OK;
     p2s_status s0 = tc_prepare(ctx);
@@ -421,6 +425,8 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
     p.ab_fmt = ctx->tc.fmt;
     p.per = ctx->tc.split ? 2 : 1;
     p.ones = ones;
+    p.perm = perm;
+    p.pitch = beta16_pitch(g.W, perm);
     p.tiles_x = (g.W + kTile - 1) / kTile;
     p.tiles_total = p.tiles_x * g.H * n;
     const Item16 *it = (const Item16 *)ctx->tc_items.data();
@@ -459,14 +465,16 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
     return P2S_OK;
 }
 
-p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, void *beta16, cudaStream_t st) {
+p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, void *beta16, int perm,
+                         cudaStream_t st) {
     p2s_status s0 = tc_prepare(ctx);
     if (s0 != P2S_OK) return s0;
     const long long npx = (long long)n * H * W;
     const long long work = npx * kGroups;
     if (work == 0) return P2S_OK;
     ProfScope pr(ctx, st, "pack_beta16", 0.0, npx * (ctx->K * 4.0 + kGroups * 16.0));
-    pack16_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(beta, (uint4 *)beta16, npx, W, ctx->K, ctx->tc.fmt);
+    pack16_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(beta, (uint4 *)beta16, npx, W, ctx->K, ctx->tc.fmt, perm,
+                                                                 beta16_pitch(W, perm));
     P2S_CUDA(cudaGetLastError());
     return P2S_OK;
 }

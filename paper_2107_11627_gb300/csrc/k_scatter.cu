@@ -280,7 +280,9 @@ __device__ void accumulate(const Params &p, uint8_t *sm, uint32_t bar0, uint32_t
 template <int C>
 __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_constant__ Params p) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned by pointer arithmetic on the __shared__ array, so that the compiler still
+    // knows every access through `sm` is to shared memory (ld/st.shared, not generic)
+    uint8_t *sm = smem_raw + ((1024u - (uint32_t)((uintptr_t)smem_raw & 1023u)) & 1023u);
     const uint32_t sbase = ptx::smem_u32(sm);
     const uint32_t bar0 = sbase + kOffBar;
     uint32_t *tmem_holder = (uint32_t *)(sm + kOffMisc);

@@ -126,7 +126,9 @@ template <int C, int BAND>
 __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constant__ Params p) {
     using L = Lay<BAND>;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned by pointer arithmetic on the __shared__ array, so that the compiler still
+    // knows every access through `sm` is to shared memory (ld/st.shared, not generic)
+    uint8_t *sm = smem_raw + ((1024u - (uint32_t)((uintptr_t)smem_raw & 1023u)) & 1023u);
     const uint32_t sbase = ptx::smem_u32(sm);
     uint2 *x16 = (uint2 *)(sm + L::OffX);
     float *sbias = (float *)(sm + L::OffBias);
@@ -652,6 +654,21 @@ p2s_status tc_prepare(p2s_ctx *ctx) {
             return basis_row(k, ty * kTaps + tx);
         });
     add_image(kLastN, kKP, [&](int n, int k) { return n < kTaps ? basis_row(k, (kTaps - 1) * kTaps + n) : (uint16_t)0; });
+    // The same chunks for the split gather kernel (k_gather.cu), columns ordered for
+    // its 16x256b TMEM fragments: column n = 8 B + 2 j + e, 8-column block B.
+    //   main chunk c: B = 6 m + 2 u + v -> tap column 3 c + u, tap row 16 m + 4 j + 2 v + e
+    //   last chunk:   B = 3 m + b       -> tap row 32, tap column 24 m + 6 j + 2 b + e (0 beyond 32)
+    for (int c = 0; c < kMainChunks; ++c)
+        add_image(kMainN, kKP, [&](int n, int k) {
+            const int B = n / 8, j = (n % 8) / 2, e = n % 2;
+            const int m = B / 6, u = (B % 6) / 2, v = B % 2;
+            return basis_row(k, (16 * m + 4 * j + 2 * v + e) * kTaps + 3 * c + u);
+        });
+    add_image(kLastN, kKP, [&](int n, int k) {
+        const int B = n / 8, j = (n % 8) / 2, e = n % 2;
+        const int tx = 24 * (B / 3) + 6 * j + 2 * (B % 3) + e;
+        return tx < kTaps ? basis_row(k, (kTaps - 1) * kTaps + tx) : (uint16_t)0;
+    });
     std::vector<float> bias(h1p + h2p, 0.f);
     for (int o = 0; o < ctx->dims[1]; ++o) bias[o] = (float)ctx->b[0][o];
     for (int o = 0; o < ctx->dims[2]; ++o) bias[h1p + o] = (float)ctx->b[1][o];

@@ -549,7 +549,8 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
         return P2S_OK;
     }
     if (option == P2S_OPT_GATHER_SPLIT) {
-        if (value != 0 && value != 1) return einval("gather split is 0 (fused) or 1 (network, then blur)");
+        if (value < 0 || value > 2)
+            return einval("gather split is 0 (fused), 1 or 2 (network, then blur; two blur kernels)");
         ctx->gather_split = value;
         return P2S_OK;
     }
@@ -600,7 +601,7 @@ p2s_status p2s_stage_mlp16(p2s_ctx *ctx, int H, int W, const float *alpha, void 
     FieldGeom g;
     p2s_status st = geometry(ctx, H, W, &g);
     if (st != P2S_OK) return st;
-    return launch_net16(ctx, g, 1, alpha, beta16, 1, ctx->d_status, (cudaStream_t)stream);
+    return launch_net16(ctx, g, 1, alpha, beta16, 1, 0, ctx->d_status, (cudaStream_t)stream);
 }
 
 p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, const p2s_image *out, void *stream) {
@@ -614,8 +615,8 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
     if ((ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) && ctx->form == P2S_SCATTER) {
         cudaStream_t s = (cudaStream_t)stream;
         void *b16 = nullptr;
-        P2S_CUDA(cudaMallocAsync(&b16, beta16_bytes(xw->H, xw->W, 1), s));
-        st = launch_pack16(ctx, xw->H, xw->W, 1, beta, b16, s);
+        P2S_CUDA(cudaMallocAsync(&b16, beta16_bytes(xw->H, xw->W, 1, 0), s));
+        st = launch_pack16(ctx, xw->H, xw->W, 1, beta, b16, 0, s);
         if (st == P2S_OK) st = launch_scatter_tc(ctx, xw->H, xw->W, xw->C, 1, ip, op, b16, ctx->d_status, s);
         cudaFreeAsync(b16, s);
         return st;
@@ -629,10 +630,13 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
             // entries 0, so the folded bias rows add nothing: beta here includes the bias)
             cudaStream_t s = (cudaStream_t)stream;
             void *b16 = nullptr;
-            P2S_CUDA(cudaMallocAsync(&b16, beta16_bytes(xw->H, xw->W, 1), s));
-            st = launch_pack16(ctx, xw->H, xw->W, 1, beta, b16, s);
+            const int perm = ctx->gather_split == 2 ? 1 : 0;
+            P2S_CUDA(cudaMallocAsync(&b16, beta16_bytes(xw->H, xw->W, 1, perm), s));
+            st = launch_pack16(ctx, xw->H, xw->W, 1, beta, b16, perm, s);
             const void *bp[1] = {b16};
-            if (st == P2S_OK) st = launch_gather_split(ctx, &f, bp, 1, xw->C, ctx->d_status, s);
+            if (st == P2S_OK)
+                st = perm ? launch_gather_frag(ctx, &f, bp, 1, xw->C, ctx->d_status, s)
+                          : launch_gather_split(ctx, &f, bp, 1, xw->C, ctx->d_status, s);
             cudaFreeAsync(b16, s);
             return st;
         }
@@ -700,7 +704,7 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
     // bound the FP32 path's beta scratch to ~1 GiB per launch group
     int chunk = kMaxBatch;
     const bool tc_scatter = tc && ctx->form == P2S_SCATTER;
-    const size_t beta_px = tc_scatter ? beta16_bytes(H, W, 1) : tc ? 0 : npx * ctx->K * sizeof(float);
+    const size_t beta_px = tc_scatter ? beta16_bytes(H, W, 1, 0) : tc ? 0 : npx * ctx->K * sizeof(float);
     const size_t beta_cap = tc_scatter ? (4ull << 30) : (1ull << 30);
     while (chunk > 1 && (size_t)chunk * beta_px > beta_cap) chunk /= 2;
     for (int i0 = 0; i0 < n; i0 += chunk) {
@@ -750,7 +754,7 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
         if (st == P2S_OK && !bw) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
         float *const *bop = blur_out;
         if (tc && ctx->form == P2S_SCATTER) {
-            if (st == P2S_OK) st = launch_net16(ctx, g, nb, alpha, beta, 1, ctx->d_status, s);
+            if (st == P2S_OK) st = launch_net16(ctx, g, nb, alpha, beta, 1, 0, ctx->d_status, s);
             if (st == P2S_OK) st = launch_scatter_tc(ctx, H, W, C, nb, xwp, bop, beta, ctx->d_status, s);
         } else {
             if (st == P2S_OK) st = launch_mlp_simt(ctx, g, nb, alpha, beta, s);
@@ -778,6 +782,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
     std::vector<TcFrame> tf[2];      // C = 1, C = 3
     std::vector<const void *> b16[2];  // split form: each frame's beta16
     const bool split = ctx->gather_split != 0;
+    const int perm = ctx->gather_split == 2 ? 1 : 0;  // the fragment kernel's beta layout
     struct PostWarp {
         FieldGeom g;
         int C;
@@ -817,7 +822,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             const size_t a_bytes = ((size_t)nb * g.Ah * g.Aw * kAlphaStride * sizeof(float) + 255) & ~(size_t)255;
             const size_t f_bytes = (fields_scratch_bytes(g, nb) + 255) & ~(size_t)255;
             const size_t xw_bytes = ((size_t)nb * npx * C * sizeof(float) + 255) & ~(size_t)255;
-            const size_t b_bytes = split ? beta16_bytes(H, W, nb) : 0;
+            const size_t b_bytes = split ? beta16_bytes(H, W, nb, perm) : 0;
             char *buf = (char *)sc.get(a_bytes + f_bytes + xw_bytes + b_bytes);
             if (!buf) {
                 set_error("device allocation failed for per-call scratch");
@@ -831,7 +836,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             const bool bw = ctx->blur_then_warp;
             if (st == P2S_OK && !bw) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
             char *b16buf = buf + a_bytes + f_bytes + xw_bytes;
-            if (st == P2S_OK && split) st = launch_net16(ctx, g, nb, alpha, b16buf, 1, ctx->d_status, s);
+            if (st == P2S_OK && split) st = launch_net16(ctx, g, nb, alpha, b16buf, 1, perm, ctx->d_status, s);
             for (int k = 0; k < nb; ++k) {
                 const int f = idx[i0 + k];
                 const float *a_k = alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride;
@@ -839,14 +844,15 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
                 tf[C == 3 ? 1 : 0].push_back(
                     TcFrame{bw ? ip[k] : xwm[k], bw ? xwm[k] : out[f].data, a_k, H, W, g.Ah, g.Aw, 0, 0, 0});
                 if (bw) post_warp.push_back(PostWarp{g, C, xwm[k], a_k, out[f].data});
-                if (split) b16[C == 3 ? 1 : 0].push_back(b16buf + (size_t)k * beta16_bytes(H, W, 1));
+                if (split) b16[C == 3 ? 1 : 0].push_back(b16buf + (size_t)k * beta16_bytes(H, W, 1, perm));
             }
         }
     }
     for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
         if (tf[ci].empty()) continue;
         const int C = ci ? 3 : 1;
-        st = split ? launch_gather_split(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
+        st = perm    ? launch_gather_frag(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
+             : split ? launch_gather_split(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
                    : launch_tc(ctx, kTcFull, tf[ci].data(), (int)tf[ci].size(), C, nullptr, nullptr, ctx->d_status, s);
     }
     for (const PostWarp &w : post_warp) {
@@ -1022,7 +1028,7 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     std::vector<int> cand;
     if (tc && ctx->form == P2S_GATHER) {
         option = P2S_OPT_GATHER_SPLIT;
-        cand = {0, 1};
+        cand = {0, 1, 2};
     } else if (tc && ctx->form == P2S_SCATTER) {
         option = P2S_OPT_SCATTER_SEGMENT_ROWS;
         cand = {32, 64, 128, 256, 1024};

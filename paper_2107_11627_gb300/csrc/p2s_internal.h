@@ -183,17 +183,28 @@ constexpr int kMaxTcFrames = 256;  // frames per persistent launch (the table is
 // wrote (launch_net16 with the bias-fold ones); beta16[i] is frame i's.
 p2s_status launch_gather_split(p2s_ctx *ctx, const TcFrame *frames, const void *const *beta16, int n, int C,
                                int *status, cudaStream_t st);
+// The fragment variant (P2S_OPT_GATHER_SPLIT = 2): beta16 in the permuted layout (perm = 1).
+p2s_status launch_gather_frag(p2s_ctx *ctx, const TcFrame *frames, const void *const *beta16, int n, int C,
+                              int *status, cudaStream_t st);
 p2s_status launch_tc(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
                      float *beta_out, int *status, cudaStream_t st);
 constexpr int kTcFull = 0, kTcMlpOnly = 1, kTcBlurOnly = 2;
 
 // Network kernel: beta of n frames into the 16-bit operand layout
-// [frame][row][14][col][8]; `ones` sets entries K, K + 1 (folded bias).
-size_t beta16_bytes(int H, int W, int n);
-p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones,
+// [frame][row][14][pos][8]; `ones` sets entries K, K + 1 (folded bias).
+// perm = 0: pos = column, row pitch W (the layout the scatter kernel and
+// p2s_stage_mlp16 use).  perm = 1 (the split gather kernel's): row pitch W
+// rounded up to 32, and within each 32-column block column c sits at
+// position 8 (c % 4) + (c % 32) / 4, so that TMEM lane L of a 32-lane
+// quadrant holds column 4 (L % 8) + L / 8 and the lanes a, a + 8, a + 16,
+// a + 24 that one thread reads through 16x256b fragments are 4 adjacent columns.
+inline int beta16_pitch(int W, int perm) { return perm ? (W + 31) & ~31 : W; }
+size_t beta16_bytes(int H, int W, int n, int perm);
+p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones, int perm,
                         int *status, cudaStream_t st);
 // FP32 beta [n][H][W][K] -> the 16-bit layout (entries k >= K zero).
-p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, void *beta16, cudaStream_t st);
+p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, void *beta16, int perm,
+                         cudaStream_t st);
 // Tensor-core scatter blur of n frames of one size from the 16-bit beta.
 p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, float *const *y,
                              const void *beta16, int *status, cudaStream_t st);

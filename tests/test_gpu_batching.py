@@ -160,20 +160,23 @@ def test_blur_then_warp_order(prec, form):
         close(ys[i].cpu().numpy(), ref.y, tol, i)
 
 
+@pytest.mark.parametrize("split_kernel", [1, 2])
 @pytest.mark.parametrize("c", [3, 1])
-def test_split_gather_matches_oracle_and_fused(c):
-    """Network kernel, then the blur-only tensor-core gather (four accumulating warps per
-    lane quadrant): the fused kernel's rounding points plus G rounded to FP16, so within
-    that rounding of it, and within the 16-bit bound of the oracle.  Sizes span several
-    tiles, a ragged column tail and an odd last row pair."""
-    shapes = [(97, 300), (33, 129), (1, 1), (64, 128)]
+def test_split_gather_matches_oracle_and_fused(c, split_kernel):
+    """Network kernel, then a blur-only tensor-core gather (1: four accumulating warps per
+    lane quadrant, one output column per thread; 2: two warps per quadrant reading G as
+    16x256b fragments, 4 output columns per thread, beta in the permuted layout): the
+    fused kernel's rounding points plus G rounded to FP16, so within that rounding of it,
+    and within the 16-bit bound of the oracle.  Sizes span several tiles, a ragged column
+    tail (including widths that are not multiples of 32) and an odd last row pair."""
+    shapes = [(97, 300), (33, 129), (1, 1), (64, 128), (18, 45)]
     xs = _frames(shapes, c=c, first=2400)
-    dr, seeds = [1.5, 3.0, 2.0, 5.0], [71, 72, 73, 74]
+    dr, seeds = [1.5, 3.0, 2.0, 5.0, 4.0], [71, 72, 73, 74, 75]
     fused = _sim()
     fused.set_option("gather_split", 0)
     split = _sim()
-    split.set_option("gather_split", 1)
-    assert split.get_option("gather_split") == 1
+    split.set_option("gather_split", split_kernel)
+    assert split.get_option("gather_split") == split_kernel
     xd = [torch.from_numpy(x).cuda() for x in xs]
     ya = fused.simulate(xd, dr, seeds)
     yb = split.simulate(xd, dr, seeds)
@@ -190,13 +193,14 @@ def test_split_gather_matches_oracle_and_fused(c):
     assert torch.equal(alone, yb[1])
 
 
-def test_split_gather_blur_then_warp_and_graphs():
+@pytest.mark.parametrize("split_kernel", [1, 2])
+def test_split_gather_blur_then_warp_and_graphs(split_kernel):
     shapes = [(96, 160), (70, 130)]
     xs = [torch.from_numpy(x).cuda() for x in _frames(shapes, first=2500)]
     a = _sim()
     b = _sim(graphs=True)
     for s in (a, b):
-        s.set_option("gather_split", 1)
+        s.set_option("gather_split", split_kernel)
         s.set_option("blur_then_warp", 1)
     ya = a.simulate(xs, [2.0, 4.0], [5, 6])
     yb = b.simulate(xs, [2.0, 4.0], [5, 6])

@@ -49,12 +49,12 @@ def test_tc_network_stage(prec, h, w):
     close(beta, ref, TOL_BF16)
 
 
-@pytest.mark.parametrize("split", [1, 0])
+@pytest.mark.parametrize("split", [1, 2, 0])
 @pytest.mark.parametrize("c", [3, 1])
 @pytest.mark.parametrize("h,w", [(40, 130), (33, 64), (1, 1), (70, 300)])
 def test_tc_blur_stage_fp16(c, h, w, split):
-    """Both gather kernels: the blur-only one fed by the network kernel's 16-bit beta
-    (split = 1, the default) and the fused one (split = 0)."""
+    """Every gather kernel: the two blur-only ones fed 16-bit beta (split = 1, the
+    default, and split = 2, the fragment kernel) and the fused one (split = 0)."""
     sim = _sim("fp16")
     sim.set_option("gather_split", split)
     rng = np.random.default_rng(31)
@@ -89,7 +89,7 @@ def _gather_rounded_g(x, beta, Hb, th, tw, g_round):
     return y
 
 
-@pytest.mark.parametrize("split", [1, 0])
+@pytest.mark.parametrize("split", [1, 2, 0])
 def test_tc_blur_stage_bf16_rounding_points(split):
     """BF16 operands: each gather kernel must round exactly beta and H to BF16 and the
     staged x_w window to FP16 (checked against the oracle with those three tensors
