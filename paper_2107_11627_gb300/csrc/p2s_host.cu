@@ -549,8 +549,8 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
         return P2S_OK;
     }
     if (option == P2S_OPT_GATHER_SPLIT) {
-        if (value < 0 || value > 2)
-            return einval("gather split is 0 (fused), 1 or 2 (network, then blur; two blur kernels)");
+        if (value < 0 || value > 3)
+            return einval("gather split is 0 (fused) or 1, 2, 3 (network, then one of three blur kernels)");
         ctx->gather_split = value;
         return P2S_OK;
     }
@@ -630,13 +630,14 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
             // entries 0, so the folded bias rows add nothing: beta here includes the bias)
             cudaStream_t s = (cudaStream_t)stream;
             void *b16 = nullptr;
-            const int perm = ctx->gather_split == 2 ? 1 : 0;
+            const int perm = ctx->gather_split >= 2 ? 1 : 0;
             P2S_CUDA(cudaMallocAsync(&b16, beta16_bytes(xw->H, xw->W, 1, perm), s));
             st = launch_pack16(ctx, xw->H, xw->W, 1, beta, b16, perm, s);
             const void *bp[1] = {b16};
             if (st == P2S_OK)
-                st = perm ? launch_gather_frag(ctx, &f, bp, 1, xw->C, ctx->d_status, s)
-                          : launch_gather_split(ctx, &f, bp, 1, xw->C, ctx->d_status, s);
+                st = ctx->gather_split == 3 ? launch_gather_x32(ctx, &f, bp, 1, xw->C, ctx->d_status, s)
+                     : perm                  ? launch_gather_frag(ctx, &f, bp, 1, xw->C, ctx->d_status, s)
+                                             : launch_gather_split(ctx, &f, bp, 1, xw->C, ctx->d_status, s);
             cudaFreeAsync(b16, s);
             return st;
         }
@@ -782,7 +783,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
     std::vector<TcFrame> tf[2];      // C = 1, C = 3
     std::vector<const void *> b16[2];  // split form: each frame's beta16
     const bool split = ctx->gather_split != 0;
-    const int perm = ctx->gather_split == 2 ? 1 : 0;  // the fragment kernel's beta layout
+    const int perm = ctx->gather_split >= 2 ? 1 : 0;  // the fragment kernels' beta layout
     struct PostWarp {
         FieldGeom g;
         int C;
@@ -851,7 +852,9 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
     for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
         if (tf[ci].empty()) continue;
         const int C = ci ? 3 : 1;
-        st = perm    ? launch_gather_frag(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
+        st = ctx->gather_split == 3
+                 ? launch_gather_x32(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
+             : perm  ? launch_gather_frag(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
              : split ? launch_gather_split(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
                    : launch_tc(ctx, kTcFull, tf[ci].data(), (int)tf[ci].size(), C, nullptr, nullptr, ctx->d_status, s);
     }
@@ -1028,7 +1031,7 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     std::vector<int> cand;
     if (tc && ctx->form == P2S_GATHER) {
         option = P2S_OPT_GATHER_SPLIT;
-        cand = {0, 1, 2};
+        cand = {0, 1, 2, 3};
     } else if (tc && ctx->form == P2S_SCATTER) {
         option = P2S_OPT_SCATTER_SEGMENT_ROWS;
         cand = {32, 64, 128, 256, 1024};

@@ -186,6 +186,9 @@ p2s_status launch_gather_split(p2s_ctx *ctx, const TcFrame *frames, const void *
 // The fragment variant (P2S_OPT_GATHER_SPLIT = 2): beta16 in the permuted layout (perm = 1).
 p2s_status launch_gather_frag(p2s_ctx *ctx, const TcFrame *frames, const void *const *beta16, int n, int C,
                               int *status, cudaStream_t st);
+// The FP32-x variant (P2S_OPT_GATHER_SPLIT = 3): same beta layout, 128 x 16 tiles.
+p2s_status launch_gather_x32(p2s_ctx *ctx, const TcFrame *frames, const void *const *beta16, int n, int C,
+                             int *status, cudaStream_t st);
 p2s_status launch_tc(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
                      float *beta_out, int *status, cudaStream_t st);
 constexpr int kTcFull = 0, kTcMlpOnly = 1, kTcBlurOnly = 2;

@@ -160,7 +160,7 @@ def test_blur_then_warp_order(prec, form):
         close(ys[i].cpu().numpy(), ref.y, tol, i)
 
 
-@pytest.mark.parametrize("split_kernel", [1, 2])
+@pytest.mark.parametrize("split_kernel", [1, 2, 3])
 @pytest.mark.parametrize("c", [3, 1])
 def test_split_gather_matches_oracle_and_fused(c, split_kernel):
     """Network kernel, then a blur-only tensor-core gather (1: four accumulating warps per
@@ -193,7 +193,7 @@ def test_split_gather_matches_oracle_and_fused(c, split_kernel):
     assert torch.equal(alone, yb[1])
 
 
-@pytest.mark.parametrize("split_kernel", [1, 2])
+@pytest.mark.parametrize("split_kernel", [1, 2, 3])
 def test_split_gather_blur_then_warp_and_graphs(split_kernel):
     shapes = [(96, 160), (70, 130)]
     xs = [torch.from_numpy(x).cuda() for x in _frames(shapes, first=2500)]

@@ -49,7 +49,7 @@ def test_tc_network_stage(prec, h, w):
     close(beta, ref, TOL_BF16)
 
 
-@pytest.mark.parametrize("split", [1, 2, 0])
+@pytest.mark.parametrize("split", [1, 2, 3, 0])
 @pytest.mark.parametrize("c", [3, 1])
 @pytest.mark.parametrize("h,w", [(40, 130), (33, 64), (1, 1), (70, 300)])
 def test_tc_blur_stage_fp16(c, h, w, split):
@@ -89,12 +89,12 @@ def _gather_rounded_g(x, beta, Hb, th, tw, g_round):
     return y
 
 
-@pytest.mark.parametrize("split", [1, 2, 0])
+@pytest.mark.parametrize("split", [1, 2, 3, 0])
 def test_tc_blur_stage_bf16_rounding_points(split):
-    """BF16 operands: each gather kernel must round exactly beta and H to BF16 and the
-    staged x_w window to FP16 (checked against the oracle with those three tensors
-    rounded), the split kernel also G to FP16 before the tap products; everything else
-    FP32."""
+    """BF16 operands: each gather kernel must round exactly beta and H to BF16; the fused
+    kernel (0) and the FP16-x blur-only kernels (1, 2) also the staged x_w window to FP16,
+    the latter two G to FP16 before the tap products; the FP32-x kernel (3) nothing else.
+    Checked against the oracle with exactly those tensors rounded; everything else FP32."""
     sim = _sim("bf16")
     sim.set_option("gather_split", split)
     rng = np.random.default_rng(32)
@@ -102,10 +102,11 @@ def test_tc_blur_stage_bf16_rounding_points(split):
     xw = inputs.blob_image(h, w, 3, 1004)
     beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
     y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda()).cpu().numpy()
-    x16 = xw.astype(np.float16).astype(np.float64)  # round-to-nearest-even, as the kernel stages it
+    # round-to-nearest-even, as the FP16-x kernels stage it
+    x16 = xw.astype(np.float16).astype(np.float64) if split != 3 else xw.astype(np.float64)
     bb, hb = bf16(beta), bf16(cfg2()["H"])
     emu = oracle.blur.gather(x16, bb, hb, 33, 33)
-    if split:
+    if split in (1, 2):
         # the emulation without its rounding is the oracle's gather itself
         assert rel(_gather_rounded_g(x16, bb, hb, 33, 33, lambda g: g), emu) < 1e-12
         emu = _gather_rounded_g(x16, bb, hb, 33, 33, lambda g: g.astype(np.float16).astype(np.float64))
