@@ -33,11 +33,88 @@ N_FRAMES, HW, CH, K, TAPS, N_DICT = 64, 512, 3, 100, 33, 50_000
 DIMS = [33, 128, 128, 100]
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-# DRAM bytes per 512x512 RGB frame of each kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
+# DRAM bytes per 512x512 RGB frame of a kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
 # 8-frame launch under ncu, divided by 8: the traffic is proportional to the frames, 16-bit beta and
-# x_w exceeding L2 already at 8 frames); valid for the kernels as measured, see profiles/
-DRAM_BYTES_PER_FRAME = {"blur_tc_scatter": (505461760 + 20555520) / 8, "blur_tc_gather16": (495983360 + 20459520) / 8,
-                        "net_tc": (5736960 + 405038848) / 8}
+# x_w exceeding L2 already at 8 frames).  Each figure holds for the kernel source it was measured
+# on (sha1 prefix of the file); a changed source reports traffic null until it is measured again.
+TRAFFIC = {
+    "blur_tc_gather16": {"bytes_per_frame": (495875840 + 24105216) / 8, "source": "k_gather.cu", "sha1": "f23e6222e865"},
+    "net_tc": {"bytes_per_frame": (5707008 + 408403712) / 8, "source": "k_net.cu", "sha1": "86d4e4205d07"},
+}
+# the blur kernels: tensor flops 2 K T per pixel (the contraction; the fused kernel adds the
+# network's), tap accumulation 2 C T FP32 flops per pixel on the FMA pipe
+BLUR_KERNELS = ("blur_tc_gather16", "blur_tc_gather16f", "blur_tc_gather_x32", "fused_tc_gather", "blur_tc_scatter")
+
+
+def source_sha1(name: str) -> str:
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_2107_11627_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def roofline(kstats, peaks, peak_src, clk, px_per_launch, C, taps):
+    """Roofline of the dominant kernel (by time in the timed region) and of every kernel.
+
+    The tensor peak is the burst figure when the clocks sampled in the timed region sat at
+    the maximum SM clock (a short region at full clock), the sustained one otherwise.  For a
+    blur kernel the three-roof bound max(tensor, FP32-pipe tap accumulation, HBM) is added;
+    the FP32 peak is 152 SMs x 128 FMA lanes x 2 flop x the sampled SM clock."""
+    if not kstats:
+        return None, []
+    mhz = clk["sm_mhz"] if clk else SM_MAX_MHZ
+    at_max = bool(clk) and clk["sm_mhz"] >= 0.97 * clk["sm_max_mhz"]
+    tc_key = "bf16_tflops" if at_max else "bf16_tflops_sustained"
+    tc_peak = peaks[tc_key]
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    hbm = peaks["hbm_gbs"]
+    per_kernel = []
+    for s_ in kstats:
+        avg_s = s_["total_ms"] / 1e3 / s_["launches"]
+        e = {"kernel": s_["name"], "ms_per_launch": avg_s * 1e3}
+        if s_["bytes"] > 0:
+            gbs = s_["bytes"] / s_["launches"] / avg_s / 1e9
+            e["achieved_gbs"], e["hbm_frac"] = gbs, gbs / hbm
+        if s_["flops"] > 0 and "fp32" not in s_["name"] and s_["name"] != "fields_colour":
+            tf = s_["flops"] / s_["launches"] / avg_s / 1e12
+            e["achieved_tflops"], e["tensor_frac"] = tf, tf / tc_peak
+        per_kernel.append(e)
+    dom = max(kstats, key=lambda s_: s_["total_ms"])
+    avg_s = dom["total_ms"] / 1e3 / dom["launches"]
+    name = dom["name"]
+    if "fp32" in name:
+        achieved = dom["flops"] / dom["launches"] / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": name,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (sampled)"}
+        return roof, per_kernel
+    if dom["flops"] <= 0:
+        achieved = dom["bytes"] / dom["launches"] / avg_s / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": name, "peak_source": f"{peak_src} hbm_gbs"}, per_kernel
+    achieved = dom["flops"] / dom["launches"] / avg_s / 1e12
+    t = TRAFFIC.get(name)
+    traffic, note = None, "no ncu DRAM figure for this kernel"
+    if t is not None and px_per_launch == N_FRAMES * 512 * 512:
+        if source_sha1(t["source"]) == t["sha1"]:
+            traffic, note = t["bytes_per_frame"] * N_FRAMES, "ncu, 8-frame launch scaled to the launch's frames"
+        else:
+            note = f"{t['source']} changed since its DRAM bytes were measured"
+    roof = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+            "frac": achieved / tc_peak, "traffic": traffic, "traffic_unit": "bytes per launch", "traffic_note": note,
+            "kernel": name, "peak_source": f"{peak_src} {tc_key} ({'clocks at max' if at_max else 'below max clock'})"}
+    if name in BLUR_KERNELS:
+        T = taps * taps
+        t_tc = dom["flops"] / dom["launches"] / (tc_peak * 1e12)
+        t_fp32 = 2.0 * C * T * px_per_launch / (fp32_peak * 1e12)
+        t_hbm = dom["bytes"] / dom["launches"] / (hbm * 1e9)
+        roofs = {"tensor": t_tc, "fp32_taps": t_fp32, "hbm": t_hbm}
+        bound = max(roofs, key=roofs.get)
+        roof["three_roof"] = {"tensor_ms": t_tc * 1e3, "fp32_taps_ms": t_fp32 * 1e3, "hbm_ms": t_hbm * 1e3,
+                              "bound": bound, "roof_ms": roofs[bound] * 1e3, "measured_ms": avg_s * 1e3,
+                              "frac": roofs[bound] / avg_s, "fp32_peak_tflops": fp32_peak}
+    return roof, per_kernel
 
 
 def workload_name(precision: str, form: str) -> str:
@@ -276,6 +353,50 @@ def run_serving(args, Hb, layers, rate=200.0, seconds=4.0, saturate=256):
             "latency_includes": "host->device copy, path, device->host copy"}
 
 
+def run_bf16_line(args, Hb, layers, xs, ys, xs_host, dr, seeds, local):
+    """The contract's BF16 path on the same workload: BF16 operands for the network and the
+    contraction, scatter form (the form whose BF16 error stays inside 2e-3 of the FP64
+    oracle; the gather form's per-output-pixel coefficients put BF16 above it), timed like
+    the headline with its own roofline and clocks, frame 0 checked against the oracle."""
+    import torch
+
+    from paper_2107_11627_gb300 import p2s
+
+    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,), precision="bf16",
+                        form="scatter")
+    for _ in range(args.warmup):
+        sim.simulate(xs, dr, seeds, out=ys)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    sim.profile(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    clocks.start()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        sim.simulate(xs, dr, seeds, out=ys)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sim.profile(False)
+    sim.check()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    kstats = sim.profile_read()
+    peaks, peak_src = load_peaks()
+    roof, kroofs = roofline(kstats, peaks, peak_src, clk, N_FRAMES * HW * HW, CH, TAPS)
+    out = {"precision": "bf16", "form": "scatter", "value": N_FRAMES / (ms / 1e3), "unit": "frames/s",
+           "mpix_per_s": N_FRAMES * HW * HW / 1e6 / (ms / 1e3), "ms_per_step": ms, "steps": args.steps,
+           "roofline": roof, "kernel_roofs": kroofs, "clocks": clk,
+           "gpu_launches": sum(k["launches"] for k in kstats)}
+    if not args.no_cpu_baseline:
+        _, y_ref = oracle_frame(Hb, layers, xs_host[0], float(dr[0]), int(seeds[0]), form="scatter")
+        err = ys[0].cpu().numpy().astype(np.float64) - y_ref
+        out["accuracy"] = {"frame": 0, "vs": "FP64 oracle", "rel_l2": float(np.linalg.norm(err) / np.linalg.norm(y_ref)),
+                           "max_abs": float(np.abs(err).max()), "tol_rel_l2": 2e-3}
+    sim.close()
+    return out
+
+
 def fp32_batched_fps(Hb, layers, frames=8):
     """The plain FP32 batched path at 512^2 RGB (scatter form), for comparison with serving."""
     import torch
@@ -312,6 +433,7 @@ def main():
     ap.add_argument("--frames", type=int, default=64, help="frames per step (profiling runs only)")
     ap.add_argument("--no-batching", action="store_true", help="skip the uneven-size batching workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
+    ap.add_argument("--no-bf16-line", action="store_true", help="skip the BF16 (scatter) line of an FP16 run")
     ap.add_argument("--gather-split", type=int, default=None,
                     help="tensor-core gather kernel: 0 fused, 1 or 2 blur-only (default: the library's)")
     args = ap.parse_args()
@@ -374,30 +496,7 @@ def main():
 
     # roofline of the dominant kernel, from its own launches in the timed region
     peaks, peak_src = load_peaks()
-    dom = max(kstats, key=lambda s: s["total_ms"]) if kstats else None
-    roof = None
-    if dom is not None:
-        avg_s = dom["total_ms"] / 1e3 / dom["launches"]
-        if "fp32" in dom["name"]:
-            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-            achieved = dom["flops"] / dom["launches"] / avg_s / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": dom["name"],
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
-        elif dom["flops"] > 0:
-            peak = peaks["bf16_tflops_sustained"]
-            achieved = dom["flops"] / dom["launches"] / avg_s / 1e12
-            tb = DRAM_BYTES_PER_FRAME.get(dom["name"])
-            traffic = tb * N_FRAMES if (tb is not None and HW == 512) else None
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu)",
-                    "kernel": dom["name"],
-                    "peak_source": f"{peak_src} bf16_tflops_sustained"}
-        else:
-            peak = peaks["hbm_gbs"]
-            achieved = dom["bytes"] / dom["launches"] / avg_s / 1e9
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": dom["name"], "peak_source": f"{peak_src} hbm_gbs"}
+    roof, kernel_roofs = roofline(kstats, peaks, peak_src, clk, N_FRAMES * HW * HW, CH, TAPS)
     launches = sum(s["launches"] for s in kstats)
 
     # end to end through the host-buffer entry point: H2D + path + D2H inside the timed region
@@ -429,6 +528,10 @@ def main():
         acc = {"frame": 0, "vs": "FP64 oracle", "rel_l2": float(np.linalg.norm(err) / np.linalg.norm(y_ref)),
                "max_abs": float(np.abs(err).max())}
 
+    bf16_line = None
+    if rank == 0 and world == 1 and args.precision == "fp16" and not args.no_bf16_line:
+        bf16_line = run_bf16_line(args, Hb, layers, xs, ys, xs_host, dr, seeds, local)
+
     batching = serving = None
     tc_path = args.precision in ("fp16", "bf16")
     if rank == 0 and world == 1 and tc_path and not args.no_batching:
@@ -450,7 +553,7 @@ def main():
                 "latency_ms": {"step_p50": float(np.percentile(step_ms, 50)),
                                "step_p99": float(np.percentile(step_ms, 99)),
                                "frame_p50": float(np.percentile(step_ms, 50)) / N_FRAMES},
-                "roofline": roof, "cpu_baseline": cpu, "accuracy": acc, "batching": batching, "serving": serving, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "roofline": roof, "kernel_roofs": kernel_roofs, "bf16": bf16_line, "cpu_baseline": cpu, "accuracy": acc, "batching": batching, "serving": serving, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in kstats]}
         print(json.dumps(line), flush=True)
     sim.close()

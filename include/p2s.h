@@ -186,6 +186,17 @@ p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *
  * k = K and K + 1 are 1.0, entries beyond are 0.  EUNSUPPORTED for FP32. */
 p2s_status p2s_stage_mlp16(p2s_ctx *ctx, int H, int W, const float *alpha, void *beta16, void *stream);
 
+/* FP8 E4M3 contexts (no counterpart in the paper, which does not state a
+ * precision): the power-of-two scales of the contraction.  The contraction
+ * G = sum_k beta_k H_k (Sec. 3.1, Eq. 4-5) runs with beta_k stored as
+ * beta_k * scale[k] and basis row k as H_k * 2^c / scale[k], each as an E4M3
+ * hi/lo pair (hi = e4m3(v), lo = e4m3(v - hi)); the tap sums are multiplied by
+ * *inv_c = 2^-c.  Entries K and K + 1 are the two columns that carry the folded
+ * last-layer bias.  scale: host array of n >= K + 2 floats, written.  EINVAL
+ * for NULL pointers or n < K + 2, EUNSUPPORTED for other precisions.
+ * Synchronous: reads the scales back from the device. */
+p2s_status p2s_contraction_scales(p2s_ctx *ctx, float *scale, int n, float *inv_c);
+
 /* Step 5 alone: y = blur of x_w with per-pixel weights beta (device float32
  * [H][W][K]) in the context's form and precision (beta is rounded to the
  * operand type first).  FP16 / BF16 gather contexts run the same blur kernel

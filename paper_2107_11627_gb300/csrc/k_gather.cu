@@ -46,14 +46,18 @@ constexpr int kChunks = kMainChunks + 1;
 constexpr int kSlot = 32768;
 constexpr int kSlots = 2;
 constexpr int kGroups = 14;                       // beta16 k-groups
+constexpr int kGroups8 = 16;                      // FP8 beta: 8 hi + 8 lo groups of 16 k
 constexpr int kGroupsEpi = 4;                     // accumulating groups of 4 warps
 constexpr int kEpi = 128 * kGroupsEpi;            // 512
 constexpr int kThreads = 64 + kEpi + 32;          // 608: + the second MMA warp (row 1)
 constexpr int kMmaWarp1 = (64 + kEpi) / 32;       // 18
 constexpr int kXPairs = kTR / 2 + 1;              // x tile rows (2 j - 1, 2 j), j = 0 .. 32
-constexpr int kBetaRow = kGroups * kStrip * 16;   // 28,672 B per staged row
+constexpr int kBetaRow = kGroups8 * kStrip * 16;  // 32,768 B per staged row (the FP8 layout's 16 groups)
 
-__host__ __device__ constexpr uint32_t colBeta(int r) { return r ? 56u : 0u; }
+// beta of output row r in TMEM: 56 columns of 16-bit values (K = 112), or 64 of E4M3
+// (hi in the first 32, lo in the next 32; K = 128)
+template <bool F8>
+__host__ __device__ constexpr uint32_t colBeta(int r) { return r ? (F8 ? 64u : 56u) : 0u; }
 __host__ __device__ constexpr uint32_t colDB(int h) { return h ? 320u : 128u; }
 
 constexpr int kOffRing = 0;
@@ -74,7 +78,7 @@ struct Item {
 struct Frame {
     const float *xw;
     float *y;
-    const uint4 *beta16;  // [H][14][W] 16-byte groups
+    const uint4 *beta16;  // [H][14][W] 16-byte groups ([H][16][W], hi then lo, in FP8 contexts)
     int H, W, tiles_x, tiles_y, tile_base;
 };
 constexpr int kMaxFrames = 256;
@@ -85,6 +89,7 @@ struct Params {
     const uint8_t *stream;  // basis chunk images
     Item item[kChunks];
     int ab_fmt;
+    float inv_c;  // FP8: the tensor core's G is 2^c G, so the tap sums are multiplied by 2^-c
     int *status;
 };
 static_assert(sizeof(Params) <= 32000, "kernel parameter block");
@@ -197,8 +202,9 @@ __device__ __forceinline__ void accumulate_pair(const Params &p, const uint4 *xp
     }
 }
 
-template <int C>
+template <int C, bool F8>
 __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_constant__ Params p) {
+    constexpr int NG = F8 ? kGroups8 : kGroups;  // beta groups staged per row
     extern __shared__ uint8_t smem_raw[];
     // aligned by pointer arithmetic on the __shared__ array, so that the compiler still
     // knows every access through `sm` is to shared memory (ld/st.shared, not generic)
@@ -261,11 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                     if (wait_bar(BAR(kBFree), (pairs & 1) ^ 1, ctl, 1)) {
                         const int r0 = tyy * kBand + 2 * rp;
                         const int nrow = min(2, F.H - r0);
-                        ptx::mbar_arrive_tx(BAR(kBStaged), (uint32_t)nrow * kGroups * cols * 16);
+                        ptx::mbar_arrive_tx(BAR(kBStaged), (uint32_t)nrow * NG * cols * 16);
                         for (int i = 0; i < nrow; ++i)
-                            for (int g = 0; g < kGroups; ++g)
+                            for (int g = 0; g < NG; ++g)
                                 ptx::bulk_g2s(sbase + kOffBeta + i * kBetaRow + g * kStrip * 16,
-                                              F.beta16 + ((size_t)(r0 + i) * kGroups + g) * F.W + c0, cols * 16,
+                                              F.beta16 + ((size_t)(r0 + i) * NG + g) * F.W + c0, cols * 16,
                                               BAR(kBStaged));
                     }
                     for (int c = 0; c < kChunks; ++c, ++it) {
@@ -299,8 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                     ptx::fence_after();
                     if (staged) {
 #pragma unroll
-                        for (int g = 0; g < kGroups; ++g)
-                            ptx::tmem_cp_128x128b(tmem + colBeta(row) + 4 * g,
+                        for (int g = 0; g < NG; ++g)
+                            ptx::tmem_cp_128x128b(tmem + colBeta<F8>(row) + 4 * g,
                                                   ptx::smem_desc(sbase + kOffBeta + row * kBetaRow + g * kStrip * 16, 16, 128));
                     }
                     ptx::mma_commit(BAR(kBFree));
@@ -318,10 +324,22 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                             const uint32_t idesc = (n == (uint32_t)kMainN) ? idesc_n96 : idesc_n48;
                             const uint64_t bd = ptx::smem_desc(sbase + kOffRing + slot * kSlot, n * 16, 128);
                             const uint64_t bstep = (uint64_t)(2 * n);
-                            const uint32_t d = tmem + colDB(h) + row * kMainN, a = tmem + colBeta(row);
+                            const uint32_t d = tmem + colDB(h) + row * kMainN, a = tmem + colBeta<F8>(row);
+                            if (F8) {
+                                // G = b_hi H_hi + b_lo H_hi + b_hi H_lo: 3 products x 4 K-steps of 32;
+                                // the lo basis image follows the hi one (n rows x 128 bytes)
+                                const uint64_t bd_lo = ptx::smem_desc(sbase + kOffRing + slot * kSlot + n * 128, n * 16, 128);
 #pragma unroll
-                            for (int ks = 0; ks < kKSteps; ++ks)
-                                ptx::mma_ts(d, a + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
+                                for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+                                    for (int ks = 0; ks < 4; ++ks)
+                                        ptx::mma_ts_f8(d, a + (pr == 1 ? 32 : 0) + ks * 8, (pr == 2 ? bd_lo : bd) + ks * bstep,
+                                                       idesc, (pr > 0 || ks > 0) ? 1u : 0u);
+                            } else {
+#pragma unroll
+                                for (int ks = 0; ks < kKSteps; ++ks)
+                                    ptx::mma_ts(d, a + ks * 8, bd + ks * bstep, idesc, ks > 0 ? 1u : 0u);
+                            }
                         }
                         ptx::mma_commit(BAR(kEmpty0 + slot));
                         ptx::mma_commit(BAR(kDFull0 + h));
@@ -394,9 +412,12 @@ __global__ void __launch_bounds__(kThreads, 1) gather_kernel(const __grid_consta
                         if (orow < F.H && c0 + col < F.W) {
                             float *o = F.y + ((size_t)orow * F.W + c0 + col) * C;
 #pragma unroll
-                            for (int ch = 0; ch < C; ++ch)
-                                o[ch] = acc[i][ch] + xchg[col * 6 + i * 3 + ch] + xchg[kStrip * 6 + col * 6 + i * 3 + ch] +
-                                        xchg[2 * kStrip * 6 + col * 6 + i * 3 + ch];
+                            for (int ch = 0; ch < C; ++ch) {
+                                const float v = acc[i][ch] + xchg[col * 6 + i * 3 + ch] +
+                                                xchg[kStrip * 6 + col * 6 + i * 3 + ch] +
+                                                xchg[2 * kStrip * 6 + col * 6 + i * 3 + ch];
+                                o[ch] = F8 ? v * p.inv_c : v;
+                            }
                         }
                     }
                 }
@@ -444,25 +465,37 @@ p2s_status launch_gather_split(p2s_ctx *ctx, const TcFrame *frames, const void *
         }
         p.n_frames = nb;
         p.tiles_total = tiles;
-        p.stream = (const uint8_t *)ctx->tc.d_H;
-        const Item16 *items = (const Item16 *)ctx->tc_items.data();
-        for (int c = 0; c < kChunks; ++c) {
-            const Item16 &it = items[6 + c];
-            p.item[c] = Item{it.offset, it.bytes, it.n, it.k};
+        const bool f8 = ctx->prec == P2S_FP8E4M3;
+        if (f8) {
+            // E4M3 hi/lo basis images (one item per chunk: hi image then lo image)
+            p.stream = (const uint8_t *)ctx->tc.d_H8;
+            for (int c = 0; c < kChunks; ++c)
+                p.item[c] = Item{ctx->tc.item8_off[c], ctx->tc.item8_bytes[c], ctx->tc.item8_n[c], 128};
+            p.inv_c = ctx->tc.inv_c8;
+        } else {
+            p.stream = (const uint8_t *)ctx->tc.d_H;
+            const Item16 *items = (const Item16 *)ctx->tc_items.data();
+            for (int c = 0; c < kChunks; ++c) {
+                const Item16 &it = items[6 + c];
+                p.item[c] = Item{it.offset, it.bytes, it.n, it.k};
+            }
+            p.inv_c = 1.f;
         }
-        p.ab_fmt = ctx->tc.fmt;
+        p.ab_fmt = f8 ? 0 : ctx->tc.fmt;  // E4M3 is type 0 of .kind::f8f6f4, FP16 type 0 of .kind::f16
         p.status = status;
         int sms = 148;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
         const int grid = tiles < sms ? tiles : sms;
-        ProfScope pr(ctx, st, "blur_tc_gather16", 2.0 * ctx->K * ctx->T * npx, npx * (C * 8.0 + kGroups * 16.0));
-        if (C == 3) {
-            P2S_CUDA(cudaFuncSetAttribute(gather_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-            gather_kernel<3><<<grid, kThreads, kSmemBytes, st>>>(p);
-        } else {
-            P2S_CUDA(cudaFuncSetAttribute(gather_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-            gather_kernel<1><<<grid, kThreads, kSmemBytes, st>>>(p);
-        }
+        ProfScope pr(ctx, st, f8 ? "blur_tc_gather8" : "blur_tc_gather16", 2.0 * ctx->K * ctx->T * npx,
+                     npx * (C * 8.0 + (f8 ? kGroups8 : kGroups) * 16.0));
+        auto run = [&](auto kern) -> p2s_status {
+            P2S_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+            kern<<<grid, kThreads, kSmemBytes, st>>>(p);
+            return P2S_OK;
+        };
+        p2s_status rs = C == 3 ? (f8 ? run(gather_kernel<3, true>) : run(gather_kernel<3, false>))
+                               : (f8 ? run(gather_kernel<1, true>) : run(gather_kernel<1, false>));
+        if (rs != P2S_OK) return rs;
         P2S_CUDA(cudaGetLastError());
     }
     return P2S_OK;

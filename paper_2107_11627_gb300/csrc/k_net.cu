@@ -45,6 +45,7 @@ constexpr int kMaxSlots = 4;
 constexpr int kThreads = kMaxSlots * 160;        // per slot: four converting warps and one MMA warp
 constexpr int kK1 = 48;                         // layer-1 depth: 33 modes padded
 constexpr int kGroups = 14;                     // beta16 k-groups of 8 (K padded to 112)
+constexpr int kGroups8 = 16;                    // FP8 beta: 8 hi + 8 lo groups of 16 k (K padded to 128)
 constexpr int kABytes = kTile * 128 * 2;        // A operand of one slot: [16 k-groups][128 rows][16 B]
 constexpr int kMaxItems = 6;
 
@@ -57,6 +58,7 @@ struct Params {
     int n, H, W, s, Ah, Aw;
     float inv_s;
     int K, h1p, h2p, n3, ab_fmt, per, ones, perm, pitch;
+    const float *scale8;  // non-null: write beta as E4M3 hi/lo pairs, beta_k multiplied by scale8[k]
     int tiles_x, tiles_total, per_cta, nslots;
     uint32_t wbytes, offA, offRow, rowBytes, offBias, offBar, offMisc;
     uint32_t item_off[kMaxItems], item_bytes[kMaxItems], item_n[kMaxItems], item_k[kMaxItems], item_soff[kMaxItems];
@@ -301,6 +303,49 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
             ptx::fence_after();
             const bool store = ok && f < p.n && col < p.W;
             const int pos = p.perm ? (col & ~31) + 8 * (col & 3) + ((col & 31) >> 2) : col;
+            if (p.scale8) {
+                // FP8: k = 0 .. 127 (entries K, K + 1 are the bias columns, 1 before scaling, and
+                // k >= K + 2 have scale 0), 16 groups: hi bytes of k = 16 g .. 16 g + 15 in group g,
+                // lo bytes in group 8 + g
+                uint4 *dst8 = p.beta16 + ((size_t)(f * p.H + row) * kGroups8) * p.pitch + pos;
+#pragma unroll 1
+                for (int c32 = 0; ok && c32 < 128; c32 += 32) {
+                    uint32_t d[32];
+                    ptx::tmem_ld32(dcol + c32, d);
+                    ptx::tmem_wait_ld_dep(d);
+                    if (store) {
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            uint32_t hw[4], lw[4];
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) {  // k = c32 + 16 q + 2 jj, + 1
+                                float v2[2];
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) {
+                                    const int k = c32 + 16 * q + 2 * jj + e;
+                                    const float raw = k < p.K ? __uint_as_float(d[16 * q + 2 * jj + e])
+                                                              : ((k == p.K || k == p.K + 1) ? 1.0f : 0.0f);
+                                    v2[e] = raw * __ldg(p.scale8 + k);
+                                }
+                                uint16_t hi, lo;
+                                tcc::e4m3_hi_lo(v2[0], v2[1], hi, lo);
+                                if (jj & 1) {
+                                    hw[jj >> 1] |= (uint32_t)hi << 16;
+                                    lw[jj >> 1] |= (uint32_t)lo << 16;
+                                } else {
+                                    hw[jj >> 1] = hi;
+                                    lw[jj >> 1] = lo;
+                                }
+                            }
+                            const int g = c32 / 16 + q;
+                            dst8[(size_t)g * p.pitch] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                            dst8[(size_t)(8 + g) * p.pitch] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        }
+                    }
+                }
+                ptx::fence_before();
+                continue;
+            }
             uint4 *dst = p.beta16 + ((size_t)(f * p.H + row) * kGroups) * p.pitch + pos;
 #pragma unroll 1
             for (int c32 = 0; ok && c32 < 8 * kGroups; c32 += 32) {  // columns 112..127 are read, unused
@@ -371,9 +416,60 @@ __global__ void pack16_kernel(const float *__restrict__ beta, uint4 *__restrict_
     out[(rowf * kGroups + g) * pitch + pos] = u;
 }
 
+// FP32 beta [n][H][W][K] -> the FP8 hi/lo layout [row][16][W][16 B] (beta_k times
+// scale8[k]; k >= K zero: the given beta already includes the last layer's bias).
+__global__ void pack8_kernel(const float *__restrict__ beta, uint4 *__restrict__ out, long long npx, int W, int K,
+                             const float *__restrict__ scale8) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // (pixel, group of 16 k)
+    if (i >= npx * 8) return;
+    const long long px = i / 8;
+    const int g = (int)(i - px * 8);
+    const long long rowf = px / W;  // frame * H + row
+    const int col = (int)(px - rowf * W);
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+        float v2[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int k = 16 * g + 2 * jj + e;
+            v2[e] = k < K ? __ldg(beta + px * K + k) * __ldg(scale8 + k) : 0.f;
+        }
+        uint16_t hi, lo;
+        tcc::e4m3_hi_lo(v2[0], v2[1], hi, lo);
+        if (jj & 1) {
+            hw[jj >> 1] |= (uint32_t)hi << 16;
+            lw[jj >> 1] |= (uint32_t)lo << 16;
+        } else {
+            hw[jj >> 1] = hi;
+            lw[jj >> 1] = lo;
+        }
+    }
+    out[(rowf * kGroups8 + g) * W + col] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    out[(rowf * kGroups8 + 8 + g) * W + col] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
 }  // namespace net
 
 using namespace net;
+
+size_t beta8_bytes(int H, int W, int n) { return (size_t)n * H * W * kGroups8 * 16; }
+
+p2s_status launch_pack8(p2s_ctx *ctx, int H, int W, int n, const float *beta, void *beta8, cudaStream_t st) {
+    p2s_status s0 = tc_prepare(ctx);
+    if (s0 != P2S_OK) return s0;
+    if (!ctx->tc.d_scale8) {
+        set_error("the FP8 operand layout exists for FP8 contexts only");
+        return P2S_EUNSUPPORTED;
+    }
+    const long long npx = (long long)n * H * W;
+    if (npx == 0) return P2S_OK;
+    ProfScope pr(ctx, st, "pack_beta8", 0.0, npx * (ctx->K * 4.0 + kGroups8 * 16.0));
+    pack8_kernel<<<(unsigned)((npx * 8 + 255) / 256), 256, 0, st>>>(beta, (uint4 *)beta8, npx, W, ctx->K,
+                                                                      ctx->tc.d_scale8);
+    P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}
 
 size_t beta16_bytes(int H, int W, int n, int perm) { return (size_t)n * H * beta16_pitch(W, perm) * kGroups * 16; }
 
@@ -427,6 +523,11 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
     p.ones = ones;
     p.perm = perm;
     p.pitch = beta16_pitch(g.W, perm);
+    p.scale8 = ctx->prec == P2S_FP8E4M3 ? ctx->tc.d_scale8 : nullptr;  // FP8: the hi/lo layout (perm 0)
+    if (p.scale8 && perm) {
+        set_error("the FP8 beta layout has natural column order");
+        return P2S_EUNSUPPORTED;
+    }
     p.tiles_x = (g.W + kTile - 1) / kTile;
     p.tiles_total = p.tiles_x * g.H * n;
     const Item16 *it = (const Item16 *)ctx->tc_items.data();
@@ -453,7 +554,7 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
     const double npx = (double)g.H * g.W * n;
     double macs = 0.0;
     for (int l = 0; l < 3; ++l) macs += (double)ctx->dims[l] * ctx->dims[l + 1];
-    ProfScope pr(ctx, st, "net_tc", 2.0 * macs * npx, npx * kGroups * 16.0);
+    ProfScope pr(ctx, st, "net_tc", 2.0 * macs * npx, npx * (p.scale8 ? kGroups8 : kGroups) * 16.0);
     if (p.ab_fmt == 1) {
         P2S_CUDA(cudaFuncSetAttribute(net_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         net_kernel<1><<<grid, 160 * p.nslots, smem, st>>>(p);

@@ -226,9 +226,9 @@ p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr
     if (!(form == P2S_SCATTER || form == P2S_GATHER || form == P2S_FFT)) return einval("unknown blur form");
     if (!(precision == P2S_FP32 || precision == P2S_BF16 || precision == P2S_FP16 || precision == P2S_FP8E4M3))
         return einval("unknown precision");
-    const bool tc_prec = precision == P2S_BF16 || precision == P2S_FP16;
-    if (precision == P2S_FP8E4M3 || (form == P2S_FFT && precision != P2S_FP32)) {
-        set_error("precision/form pair not built yet");
+    const bool tc_prec = tc_precision(precision);
+    if ((precision == P2S_FP8E4M3 && form != P2S_GATHER) || (form == P2S_FFT && precision != P2S_FP32)) {
+        set_error("precision/form pair not built (FP8 E4M3: gather form only; FFT: FP32 only)");
         return P2S_EUNSUPPORTED;
     }
 
@@ -275,6 +275,7 @@ p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr
     }
     std::vector<float> Lf(kModes * kModes);
     for (int i = 0; i < kModes * kModes; ++i) Lf[i] = (float)R[i];
+    ctx->L64.assign(R.begin(), R.end());
 
     // FP32 device copies used by the plain path.
     std::vector<float> H32(ctx->H.begin(), ctx->H.end()), Ht32((size_t)ctx->T * ctx->K);
@@ -356,6 +357,8 @@ void p2s_destroy(p2s_ctx *ctx) {
     cudaFree(ctx->tc.d_H);
     cudaFree(ctx->tc.d_bias);
     cudaFree(ctx->tc.d_Hs);
+    cudaFree(ctx->tc.d_H8);
+    cudaFree(ctx->tc.d_scale8);
     for (auto &kv : ctx->fft_tw) cudaFree(kv.second);
     for (auto &kv : ctx->dense_L) cudaFree(kv.second);
     for (auto &kv : ctx->fft_basis) cudaFree(kv.second);
@@ -515,7 +518,7 @@ p2s_status p2s_stage_mlp(p2s_ctx *ctx, int H, int W, const float *alpha, float *
     FieldGeom g;
     p2s_status st = geometry(ctx, H, W, &g);
     if (st != P2S_OK) return st;
-    if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) {
+    if (tc_precision(ctx->prec)) {
         const TcFrame f{nullptr, nullptr, alpha, H, W, g.Ah, g.Aw, 0, 0, 0};
         return launch_tc(ctx, kTcMlpOnly, &f, 1, 1, nullptr, beta, ctx->d_status, (cudaStream_t)stream);
     }
@@ -551,6 +554,10 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
     if (option == P2S_OPT_GATHER_SPLIT) {
         if (value < 0 || value > 3)
             return einval("gather split is 0 (fused) or 1, 2, 3 (network, then one of three blur kernels)");
+        if (ctx->prec == P2S_FP8E4M3 && value != 1) {
+            set_error("the FP8 E4M3 contraction runs in the split gather kernel 1 only");
+            return P2S_EUNSUPPORTED;
+        }
         ctx->gather_split = value;
         return P2S_OK;
     }
@@ -604,6 +611,20 @@ p2s_status p2s_stage_mlp16(p2s_ctx *ctx, int H, int W, const float *alpha, void 
     return launch_net16(ctx, g, 1, alpha, beta16, 1, 0, ctx->d_status, (cudaStream_t)stream);
 }
 
+p2s_status p2s_contraction_scales(p2s_ctx *ctx, float *scale, int n, float *inv_c) {
+    if (!ctx || !scale || !inv_c) return einval("ctx, scale and inv_c must be non-NULL");
+    if (ctx->prec != P2S_FP8E4M3) {
+        set_error("contraction scales exist for FP8 E4M3 contexts only");
+        return P2S_EUNSUPPORTED;
+    }
+    if (n < ctx->K + 2) return einval("scale needs K + 2 entries");
+    p2s_status st = tc_prepare(ctx);
+    if (st != P2S_OK) return st;
+    P2S_CUDA(cudaMemcpy(scale, ctx->tc.d_scale8, (size_t)(ctx->K + 2) * sizeof(float), cudaMemcpyDeviceToHost));
+    *inv_c = ctx->tc.inv_c8;
+    return P2S_OK;
+}
+
 p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, const p2s_image *out, void *stream) {
     if (!ctx || !beta) return einval("ctx and beta must be non-NULL");
     p2s_status st;
@@ -612,6 +633,20 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
     if (xw->data == out->data) return einval("out must not alias xw");
     const float *ip[1] = {xw->data};
     float *op[1] = {out->data};
+    if (ctx->prec == P2S_FP8E4M3) {
+        // the FP8 layout (beta times the per-basis scales, E4M3 hi/lo), then the split gather
+        FieldGeom g;
+        if ((st = geometry(ctx, xw->H, xw->W, &g)) != P2S_OK) return st;
+        const TcFrame f{xw->data, out->data, nullptr, xw->H, xw->W, g.Ah, g.Aw, 0, 0, 0};
+        cudaStream_t s = (cudaStream_t)stream;
+        void *b8 = nullptr;
+        P2S_CUDA(cudaMallocAsync(&b8, beta8_bytes(xw->H, xw->W, 1), s));
+        st = launch_pack8(ctx, xw->H, xw->W, 1, beta, b8, s);
+        const void *bp[1] = {b8};
+        if (st == P2S_OK) st = launch_gather_split(ctx, &f, bp, 1, xw->C, ctx->d_status, s);
+        cudaFreeAsync(b8, s);
+        return st;
+    }
     if ((ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) && ctx->form == P2S_SCATTER) {
         cudaStream_t s = (cudaStream_t)stream;
         void *b16 = nullptr;
@@ -784,6 +819,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
     std::vector<const void *> b16[2];  // split form: each frame's beta16
     const bool split = ctx->gather_split != 0;
     const int perm = ctx->gather_split >= 2 ? 1 : 0;  // the fragment kernels' beta layout
+    const bool f8 = ctx->prec == P2S_FP8E4M3;          // split kernel 1 with the FP8 layout
     struct PostWarp {
         FieldGeom g;
         int C;
@@ -823,7 +859,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             const size_t a_bytes = ((size_t)nb * g.Ah * g.Aw * kAlphaStride * sizeof(float) + 255) & ~(size_t)255;
             const size_t f_bytes = (fields_scratch_bytes(g, nb) + 255) & ~(size_t)255;
             const size_t xw_bytes = ((size_t)nb * npx * C * sizeof(float) + 255) & ~(size_t)255;
-            const size_t b_bytes = split ? beta16_bytes(H, W, nb, perm) : 0;
+            const size_t b_bytes = f8 ? beta8_bytes(H, W, nb) : split ? beta16_bytes(H, W, nb, perm) : 0;
             char *buf = (char *)sc.get(a_bytes + f_bytes + xw_bytes + b_bytes);
             if (!buf) {
                 set_error("device allocation failed for per-call scratch");
@@ -845,7 +881,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
                 tf[C == 3 ? 1 : 0].push_back(
                     TcFrame{bw ? ip[k] : xwm[k], bw ? xwm[k] : out[f].data, a_k, H, W, g.Ah, g.Aw, 0, 0, 0});
                 if (bw) post_warp.push_back(PostWarp{g, C, xwm[k], a_k, out[f].data});
-                if (split) b16[C == 3 ? 1 : 0].push_back(b16buf + (size_t)k * beta16_bytes(H, W, 1, perm));
+                if (split) b16[C == 3 ? 1 : 0].push_back(b16buf + (size_t)k * (f8 ? beta8_bytes(H, W, 1) : beta16_bytes(H, W, 1, perm)));
             }
         }
     }
@@ -887,7 +923,7 @@ static p2s_status validate_simulate(p2s_ctx *ctx, const p2s_image *frames, int n
 
 static p2s_status simulate_impl(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
                                 const unsigned long long *seeds, const p2s_image *out, cudaStream_t s, Scratch &sc) {
-    if ((ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) && ctx->form == P2S_GATHER)
+    if (tc_precision(ctx->prec) && ctx->form == P2S_GATHER)
         return simulate_tc_gather(ctx, frames, out, n, d_over_r0, seeds, s, sc);
     // group frames of one shape, in order of first appearance
     std::vector<char> done(n, 0);
@@ -908,7 +944,7 @@ static p2s_status simulate_impl(p2s_ctx *ctx, const p2s_image *frames, int n, co
 
 // One-time device preparation that must not happen inside a stream capture.
 static p2s_status prepare_for_capture(p2s_ctx *ctx) {
-    if (ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) {
+    if (tc_precision(ctx->prec)) {
         p2s_status st = tc_prepare(ctx);
         if (st != P2S_OK) return st;
         if (ctx->form == P2S_SCATTER && (st = scatter_prepare(ctx)) != P2S_OK) return st;
@@ -1026,7 +1062,7 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     p2s_status st = validate_simulate(ctx, frames, n, d_over_r0, seeds, out);
     if (st != P2S_OK) return st;
     if (reps < 1) return einval("reps must be >= 1");
-    const bool tc = ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16;
+    const bool tc = ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16;  // FP8: one kernel, nothing to tune
     int option = 0;
     std::vector<int> cand;
     if (tc && ctx->form == P2S_GATHER) {

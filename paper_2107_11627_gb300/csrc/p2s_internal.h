@@ -36,6 +36,9 @@ struct FieldGeom {
     int Fh, Fw;  // torus (powers of two)
 };
 
+// Precisions that run the network and the contraction on the tensor cores.
+inline bool tc_precision(p2s_precision p) { return p == P2S_BF16 || p == P2S_FP16 || p == P2S_FP8E4M3; }
+
 // Per-launch frame parameters, passed by value.
 struct FrameBatch {
     int n;
@@ -61,6 +64,14 @@ struct TcPack {
     void *d_Hs = nullptr;  // basis for the scatter kernel, tap-column-major [14][1104][8] 16-bit
     int seg_rows = 0;      // source rows per scatter work unit (0: default)
     int band_rows = 0;     // output rows per fused gather tile: 16 or 32 (0: default 32)
+    // FP8 E4M3 contraction (P2S_FP8E4M3): basis chunk images as E4M3 hi/lo pairs, rows
+    // scaled by per-basis powers of two, in the split gather's column order (hi image
+    // then lo image per chunk); the network writes beta scaled by scale8[k] as hi/lo
+    // pairs; G comes out of the tensor core multiplied by 2^c8, undone by inv_c8.
+    void *d_H8 = nullptr;
+    float *d_scale8 = nullptr;  // [128] beta multipliers (0 beyond the bias columns)
+    float inv_c8 = 1.f;
+    uint32_t item8_off[12] = {}, item8_bytes[12] = {}, item8_n[12] = {};
 };
 
 // One B image of the tensor-core weight stream: byte offset and size in the
@@ -99,6 +110,7 @@ struct p2s_ctx {
     std::vector<double> ell;
     double kappa = 0.0;
     float *d_L = nullptr;          // FP32 lower Cholesky factor [35][35]
+    std::vector<double> L64;       // the same factor in FP64 (lower triangle used)
     int kernel_of_mode[p2s::kModes];
     int *d_kernel_of_mode = nullptr;
     std::map<int, p2s::FilterTable> tables;
@@ -205,6 +217,11 @@ inline int beta16_pitch(int W, int perm) { return perm ? (W + 31) & ~31 : W; }
 size_t beta16_bytes(int H, int W, int n, int perm);
 p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones, int perm,
                         int *status, cudaStream_t st);
+// FP8 contexts: the network kernel writes beta as E4M3 hi/lo pairs in
+// [frame][row][16][col][16 B] (groups 0..7 the hi bytes of k = 16 g .. 16 g + 15,
+// groups 8..15 the lo bytes), column order natural (perm = 0).
+size_t beta8_bytes(int H, int W, int n);
+p2s_status launch_pack8(p2s_ctx *ctx, int H, int W, int n, const float *beta, void *beta8, cudaStream_t st);
 // FP32 beta [n][H][W][K] -> the 16-bit layout (entries k >= K zero).
 p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, void *beta16, int perm,
                          cudaStream_t st);

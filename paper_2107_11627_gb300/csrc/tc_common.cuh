@@ -84,6 +84,17 @@ __device__ __forceinline__ void fma_mix_x1(uint32_t x, uint32_t gw, float &c) {
             : "+f"(c) : "r"(x), "r"(gw));
 }
 
+// v0, v1 (FP32) as E4M3 hi/lo pairs: hi = e4m3(v), lo = e4m3(v - hi) (the difference is
+// exact in FP32), both rounded to nearest even and saturated at +-448.  Each result is
+// two bytes: v0's in the low byte, v1's in the high byte.
+__device__ __forceinline__ void e4m3_hi_lo(float v0, float v1, uint16_t &hi, uint16_t &lo) {
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %2, %1;" : "=h"(hi) : "f"(v0), "f"(v1));
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(hi));
+    const float2 hv = __half22float2(*reinterpret_cast<const __half2 *>(&h2));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %2, %1;" : "=h"(lo) : "f"(v0 - hv.x), "f"(v1 - hv.y));
+}
+
 struct Ctl {
     volatile int *abort;
     int *status;

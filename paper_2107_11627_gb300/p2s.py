@@ -92,6 +92,7 @@ _SIGS = {
                                C.POINTER(p2s_tune_result)]),
     "p2s_get_option": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "p2s_stage_mlp16": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "p2s_contraction_scales": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float)]),
     "p2s_stage_blur": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
     "p2s_stage_mlp_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "p2s_noll_covariance": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
@@ -336,6 +337,15 @@ class Simulator:
         _check(lib().p2s_stage_mlp16(self.ctx, H, W, C.c_void_p(alpha.data_ptr()), C.c_void_p(out.data_ptr()),
                                      _stream_handle(stream)), "p2s_stage_mlp16")
         return out
+
+    def contraction_scales(self):
+        """FP8 contexts: (beta multipliers [K + 2] (the last two for the folded-bias columns),
+        2^-c): beta_k is stored as beta_k * scale[k], basis row k as H_k * 2^c / scale[k]."""
+        sc = np.zeros(self.K + 2, dtype=np.float32)
+        inv = C.c_float()
+        _check(lib().p2s_contraction_scales(self.ctx, sc.ctypes.data_as(C.POINTER(C.c_float)), self.K + 2,
+                                            C.byref(inv)), "p2s_contraction_scales")
+        return sc, float(inv.value)
 
     def stage_blur(self, xw, beta, stream=None):
         torch = _torch()

@@ -111,3 +111,57 @@ def train_p2s(Hb: np.ndarray, dims, n_dict: int = 50_000, taps: int = 33, epochs
         np.savez(path, report=np.array(report, dtype=object),
                  **{f"W{i}": W for i, (W, _) in enumerate(layers)}, **{f"b{i}": b for i, (_, b) in enumerate(layers)})
     return layers, report
+
+
+def network_psfs(Hb: np.ndarray, layers, alpha_hi: np.ndarray) -> np.ndarray:
+    """[n, T] PSFs H^T beta(alpha) of the network (ReLU after every layer but the last)."""
+    h = np.asarray(alpha_hi, dtype=np.float64)
+    for i, (W, b) in enumerate(layers):
+        h = h @ W.T + b
+        if i + 1 < len(layers):
+            h = np.maximum(h, 0.0)
+    return h @ Hb
+
+
+def _width(psf: np.ndarray) -> float:
+    """RMS radius (pixels) of a PSF about its centroid."""
+    n = psf.shape[0]
+    yy, xx = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
+    m = psf.sum()
+    cy, cx = (psf * yy).sum() / m, (psf * xx).sum() / m
+    return float(np.sqrt((psf * ((yy - cy) ** 2 + (xx - cx) ** 2)).sum() / m))
+
+
+def exposure_psfs(Hb: np.ndarray, layers, taps: int, d_over_r0: float, n: int = 2000, seed: int = 5,
+                  margin: int = 8, kappa: float = -4.0 / np.pi):
+    """Short- and long-exposure PSFs (Sec. 4.1, Evaluation 2) of the network against the
+    pupil-FFT PSFs it stands in for, over n draws at one turbulence strength.
+
+    SE: the mean of the centred PSFs (tilts left out), network H^T beta(alpha) against the
+    Eq. 2 PSF of the same alpha.  LE: the mean of the same PSFs each shifted by its tilt
+    displacement d = kappa (alpha_3, alpha_2) pixels (the simulator's warp), placed
+    bilinearly on a grid `margin` pixels wider on each side.  Returns the PSFs and, per
+    exposure, the relative L2 distance network vs pupil FFT and both RMS widths."""
+    D, alpha = basis.psf_dictionary(n, taps, seed=seed, dr0_range=(d_over_r0, d_over_r0), with_alpha=True)
+    P = network_psfs(Hb, layers, alpha[:, 2:])
+    out = {}
+    se_x, se_n = D.mean(axis=0).reshape(taps, taps), P.mean(axis=0).reshape(taps, taps)
+    G = taps + 2 * margin
+    le_x, le_n = np.zeros((G, G)), np.zeros((G, G))
+    dy, dx = kappa * alpha[:, 1], kappa * alpha[:, 0]
+    for i in range(n):
+        iy, ix = int(np.floor(dy[i])), int(np.floor(dx[i]))
+        fy, fx = dy[i] - iy, dx[i] - ix
+        for src, dst in ((D[i], le_x), (P[i], le_n)):
+            p = src.reshape(taps, taps)
+            for oy, wy in ((0, 1 - fy), (1, fy)):
+                for ox, wx in ((0, 1 - fx), (1, fx)):
+                    y0, x0 = margin + iy + oy, margin + ix + ox
+                    if 0 <= y0 and y0 + taps <= G and 0 <= x0 and x0 + taps <= G:
+                        dst[y0:y0 + taps, x0:x0 + taps] += wy * wx * p
+    le_x /= n
+    le_n /= n
+    for name, a, b in (("se", se_x, se_n), ("le", le_x, le_n)):
+        out[name] = {"rel_l2": float(np.linalg.norm(b - a) / np.linalg.norm(a)), "width_psf": _width(a),
+                     "width_network": _width(b), "psf": a, "network": b}
+    return out

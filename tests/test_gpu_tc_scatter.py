@@ -162,3 +162,17 @@ def test_frames_bf16_within_contract():
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form="scatter")
         close(ys[i].cpu().numpy(), ref.y, TOL_BF16, i)
+
+
+@pytest.mark.parametrize("dr", [1.5, 5.0])
+def test_full_size_frame_bf16_within_contract(dr):
+    """The contract's BF16 path on a 512 x 512 RGB frame of the benchmark workload (BF16
+    network and contraction, scatter form, FP32 fields, warp and tap sums): relative L2 and
+    max-abs against the FP64 oracle, whole frame, at weak and strong turbulence."""
+    sim = _sim("bf16")
+    x = inputs.blob_image(512, 512, 3, 1000)
+    (y,) = sim.simulate([torch.from_numpy(x).cuda()], [dr], [10**6 + 7])
+    sim.check()
+    ref = oracle.frame.simulate(x.astype(np.float64), 10**6 + 7, dr, cfg2()["H"], cfg2()["layers"],
+                                CorrParams(8, (16.0,)), (33, 33), form="scatter")
+    close(y.cpu().numpy(), ref.y, TOL_BF16, f"D/r0={dr}")
