@@ -267,9 +267,10 @@ def run_reference(args):
 SERVE_SIZES = [(256, 256), (512, 512), (576, 1024), (720, 1280), (1080, 1920), (1152, 2048)]
 
 
-def run_batching(args, Hb, layers, frames=96, steps=5):
+def run_batching(args, Hb, layers, precision, form, frames=96, steps=5):
     """96 RGB frames of uneven size (long side in {128..1024}, aspect 1..16:9), D/r0 ~ U[0.5, 6]:
-    autotuned tile shape, one persistent tensor-core launch per call, captured as a CUDA graph."""
+    autotuned kernel and tile shape, captured as a CUDA graph (the gather kernels take the
+    whole uneven batch in one persistent launch; the scatter kernel one launch per size)."""
     import torch
 
     from paper_2107_11627_gb300 import inputs, p2s
@@ -279,9 +280,10 @@ def run_batching(args, Hb, layers, frames=96, steps=5):
     ys = [torch.empty_like(x) for x in xs]
     dr = inputs.frame_strengths(frames, 0.5, 6.0, 9)
     seeds = inputs.frame_seeds(frames, 2 * 10**6)
-    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,), precision=args.precision,
-                        form=args.form)
+    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,), precision=precision,
+                        form=form)
     tune = sim.autotune(xs, dr, seeds, out=ys, reps=1)
+    tune = {**tune, "candidates": {str(k): v for k, v in tune["candidates"].items()}, "best": str(tune["best"])}
     sim.set_option("graphs", 1)
     for _ in range(2):
         sim.simulate(xs, dr, seeds, out=ys)
@@ -297,7 +299,7 @@ def run_batching(args, Hb, layers, frames=96, steps=5):
     ms = ev[0].elapsed_time(ev[1]) / steps
     mpx = sum(h * w for h, w in sizes) / 1e6
     out = {"workload": f"{frames} RGB frames of uneven size (long side 128..1024, aspect 1..16:9), "
-                       f"{args.precision} {args.form}, autotuned, CUDA graph",
+                       f"{precision} {form}, autotuned, CUDA graph", "precision": precision, "form": form,
            "frames_per_s": frames / (ms / 1e3), "mpix_per_s": mpx / (ms / 1e3), "ms_per_call": ms,
            "mpix_per_call": mpx, "autotune": tune, "graph_instantiations": sim.get_option("graph_instantiations"),
            "graph_updates": sim.get_option("graph_updates")}
@@ -305,7 +307,7 @@ def run_batching(args, Hb, layers, frames=96, steps=5):
     return out
 
 
-def run_serving(args, Hb, layers, rate=200.0, seconds=4.0, saturate=256):
+def run_serving(args, Hb, layers, precision, form, rate=200.0, seconds=30.0, saturate=256):
     """Poisson arrivals of single RGB frames (sizes 256^2 .. 2048x1152, D/r0 ~ U[0.5, 6], own seed each)
     into the request loop; p50/p99 latency from submission to result in host memory."""
     import torch
@@ -318,8 +320,8 @@ def run_serving(args, Hb, layers, rate=200.0, seconds=4.0, saturate=256):
     ring = 6
     pin_out = {hw: [torch.empty(hw + (CH,), dtype=torch.float32).pin_memory().numpy() for _ in range(ring)]
                for hw in SERVE_SIZES}
-    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,), precision=args.precision,
-                        form=args.form)
+    sim = p2s.Simulator(Hb, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,), precision=precision,
+                        form=form)
     srv = p2s.Server(sim, hbm_budget_bytes=8 << 30, max_inflight=4, max_batch=16)
 
     def drive(arrivals):
@@ -344,7 +346,8 @@ def run_serving(args, Hb, layers, rate=200.0, seconds=4.0, saturate=256):
     sim.close()
     mean_px = float(np.mean([h * w for h, w in SERVE_SIZES]))
     return {"workload": f"Poisson {rate:.0f} req/s for {seconds:.0f} s, RGB frames of "
-                        f"{'/'.join(f'{w}x{h}' for h, w in SERVE_SIZES)}, {args.precision} {args.form}",
+                        f"{'/'.join(f'{w}x{h}' for h, w in SERVE_SIZES)}, {precision} {form}",
+            "precision": precision, "form": form,
             "requests": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "frames_per_s": n / el, "saturation": {"requests": saturate, "frames_per_s": saturate / el_sat,
                                                   "mpix_per_s": saturate * mean_px / 1e6 / el_sat,
@@ -397,6 +400,35 @@ def run_bf16_line(args, Hb, layers, xs, ys, xs_host, dr, seeds, local):
     return out
 
 
+def run_spectral(args, layers, xs, ys, dr, seeds, n_dict=8000):
+    """Wavelength-dependent RGB (three PSF sets at 570, 540, 450 nm) on the headline workload
+    and precision: three single-channel passes.  The channel bases come from an n_dict-draw
+    dictionary each (throughput does not depend on the basis values)."""
+    import torch
+
+    from paper_2107_11627_gb300 import basis, p2s
+
+    bases = basis.build_basis_spectral(K, TAPS, n_dict)
+    sim = p2s.SpectralSimulator(bases, (TAPS, TAPS), layers, anchor_spacing=8, corr_len_px=(16.0,),
+                                precision=args.precision, form=args.form)
+    for _ in range(args.warmup):
+        sim.simulate(xs, dr, seeds, out=ys)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        sim.simulate(xs, dr, seeds, out=ys)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    sim.check()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    sim.close()
+    return {"workload": f"{N_FRAMES} RGB frames {HW}x{HW}, three wavelength bases (570/540/450 nm), "
+                        f"{args.precision} {args.form}", "frames_per_s": N_FRAMES / (ms / 1e3), "ms_per_step": ms,
+            "bases_from_dictionary_of": n_dict}
+
+
 def fp32_batched_fps(Hb, layers, frames=8):
     """The plain FP32 batched path at 512^2 RGB (scatter form), for comparison with serving."""
     import torch
@@ -434,6 +466,9 @@ def main():
     ap.add_argument("--no-batching", action="store_true", help="skip the uneven-size batching workload")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving workload")
     ap.add_argument("--no-bf16-line", action="store_true", help="skip the BF16 (scatter) line of an FP16 run")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="Poisson arrival window of the serving run")
+    ap.add_argument("--spectral", action="store_true",
+                    help="also time wavelength-dependent RGB (three bases, 570/540/450 nm) on the workload")
     ap.add_argument("--gather-split", type=int, default=None,
                     help="tensor-core gather kernel: 0 fused, 1 or 2 blur-only (default: the library's)")
     args = ap.parse_args()
@@ -532,13 +567,19 @@ def main():
     if rank == 0 and world == 1 and args.precision == "fp16" and not args.no_bf16_line:
         bf16_line = run_bf16_line(args, Hb, layers, xs, ys, xs_host, dr, seeds, local)
 
-    batching = serving = None
+    batching = serving = spectral = None
     tc_path = args.precision in ("fp16", "bf16")
+    # the a9 workloads on the headline path and on the contract's BF16 (scatter) path
+    paths = [(args.precision, args.form)] + ([("bf16", "scatter")] if args.precision == "fp16" else [])
     if rank == 0 and world == 1 and tc_path and not args.no_batching:
-        batching = run_batching(args, Hb, layers)
+        batching = [run_batching(args, Hb, layers, pr, fm) for pr, fm in paths]
     if rank == 0 and world == 1 and tc_path and not args.no_serving:
-        serving = run_serving(args, Hb, layers)
-        serving["fp32_batched_512_frames_per_s"] = fp32_batched_fps(Hb, layers)
+        fp32_fps = fp32_batched_fps(Hb, layers)
+        serving = [run_serving(args, Hb, layers, pr, fm, seconds=args.serve_seconds) for pr, fm in paths]
+        for sv in serving:
+            sv["fp32_batched_512_frames_per_s"] = fp32_fps
+    if rank == 0 and world == 1 and args.spectral:
+        spectral = run_spectral(args, layers, xs, ys, dr, seeds)
 
     if rank == 0:
         dtype = {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp8": "e4m3"}[args.precision]
@@ -553,7 +594,7 @@ def main():
                 "latency_ms": {"step_p50": float(np.percentile(step_ms, 50)),
                                "step_p99": float(np.percentile(step_ms, 99)),
                                "frame_p50": float(np.percentile(step_ms, 50)) / N_FRAMES},
-                "roofline": roof, "kernel_roofs": kernel_roofs, "bf16": bf16_line, "cpu_baseline": cpu, "accuracy": acc, "batching": batching, "serving": serving, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "roofline": roof, "kernel_roofs": kernel_roofs, "bf16": bf16_line, "cpu_baseline": cpu, "accuracy": acc, "batching": batching, "serving": serving, "spectral": spectral, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in kstats]}
         print(json.dumps(line), flush=True)
     sim.close()

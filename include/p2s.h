@@ -151,6 +151,22 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
  * device->host copy the path of the chunk after, on two copy streams owned by
  * the context; the path runs on `stream`.  Results equal p2s_simulate's.
  * Pinned host memory gives full copy bandwidth and overlap. */
+/* Wavelength-dependent colour (Sec. 3.5): RGB frames whose channels are blurred
+ * with three PSF sets, one per wavelength (the paper's 570, 540 and 450 nm for
+ * R, G, B), at three times the cost of one.  ctx3[c] is channel c's context:
+ * its basis holds that wavelength's PSFs, and its first network layer takes
+ * alpha in radians at that wavelength (alpha at the reference wavelength times
+ * lambda_ref / lambda_c, folded into W1 by the caller).  The three contexts
+ * must share the device, the correlation parameters, kappa and the options
+ * that shape the fields and the warp (one turbulence realisation: the fields
+ * and the achromatic tilt warp are the same in every channel).  frames / out:
+ * as for p2s_simulate, C = 3, device memory; channel c of each output is
+ * channel c of the input run through ctx3[c] as a single-channel frame.
+ * Stream-ordered scratch of two H x W planes per frame.  Errors as
+ * p2s_simulate, plus EINVAL for mismatched contexts or C != 3. */
+p2s_status p2s_simulate_spectral(p2s_ctx *const *ctx3, const p2s_image *frames, int n, const float *D_over_r0,
+                                 const unsigned long long *seeds, const p2s_image *out, void *stream);
+
 p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
                              const unsigned long long *seeds, const p2s_image *out, void *stream);
 
@@ -276,16 +292,21 @@ p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value);
 
 /* Autotuner (no counterpart in the paper).  Runs p2s_simulate on the given
  * batch (device frames, written to `out`) once per candidate setting of the
- * launch option of the context's path (P2S_OPT_GATHER_SPLIT, fused or split
- * kernels, for the tensor-core gather; P2S_OPT_SCATTER_SEGMENT_ROWS for the
- * tensor-core scatter; the FP32 path has none), after one warm-up call times `reps`
+ * launch options of the context's path, after one warm-up call times `reps`
  * calls with CUDA events on `stream` (synchronising it), keeps the fastest
  * setting in the context and reports every candidate in `res` (may be NULL).
- * Arguments as p2s_simulate; reps >= 1. */
+ * Candidates: FP16 / BF16 tensor-core gather, the kernel and its tile shape
+ * (P2S_OPT_GATHER_SPLIT 1, 2, 3 -- the three blur-only kernels, 128 x 32 and
+ * 128 x 16 tiles, one or four output columns per accumulating thread -- and 0,
+ * the fused kernel, with P2S_OPT_GATHER_BAND_ROWS 16 or 32); tensor-core
+ * scatter, P2S_OPT_SCATTER_SEGMENT_ROWS 8 .. 1024 (the rows per work unit);
+ * FP32 and FP8 paths have none.  Arguments as p2s_simulate; reps >= 1. */
 typedef struct {
     int option;       /* the p2s_option tuned (0 if the path has none) */
+    int option2;      /* a second option set with it (0 if none) */
     int n;            /* candidates tried */
-    int value[8];     /* candidate settings */
+    int value[8];     /* candidate settings of `option` */
+    int value2[8];    /* ... and of `option2` (0: left as it was) */
     float ms[8];      /* mean milliseconds per call of each */
     int best;         /* index of the setting kept */
 } p2s_tune_result;

@@ -77,15 +77,16 @@ def psf_taps(alpha_hi: np.ndarray, taps_h: int, taps_w: int, n_pupil: int = 32, 
 
 
 def dictionary(z: np.ndarray, dr0: np.ndarray, taps_h: int, taps_w: int, n_pupil: int = 32, n_fft: int = 64,
-               chunk: int = 2000) -> np.ndarray:
+               chunk: int = 2000, phase_scale: float = 1.0) -> np.ndarray:
     """N_dict x T matrix of centred PSFs.
 
     Draw i has alpha_{2..36} = dr0_i^(5/6) L z_i (L = chol(R_Z)); the tilts
-    J = 2, 3 are dropped so the PSF is centred (Sec. 3.2).
+    J = 2, 3 are dropped so the PSF is centred (Sec. 3.2).  phase_scale multiplies
+    the phase (the coefficients are in radians at another wavelength: oracle.spectral).
     """
     L = noll.cholesky_lower(noll.noll_cov(36))
     alpha = (dr0[:, None] ** (5.0 / 6.0)) * (z @ L.T)
-    hi = alpha[:, 2:]
+    hi = alpha[:, 2:] * phase_scale
     rows = []
     for s in range(0, len(hi), chunk):
         rows.append(psf_taps(hi[s : s + chunk], taps_h, taps_w, n_pupil, n_fft).reshape(-1, taps_h * taps_w))
@@ -101,7 +102,8 @@ def svd_basis(D: np.ndarray, K: int) -> np.ndarray:
     return H
 
 
-def make_basis(z: np.ndarray, dr0: np.ndarray, K: int, taps: int, n_pupil: int = 32, n_fft: int = 64):
+def make_basis(z: np.ndarray, dr0: np.ndarray, K: int, taps: int, n_pupil: int = 32, n_fft: int = 64,
+               phase_scale: float = 1.0):
     """Dictionary of the given draws -> basis.  Returns (H [K, T], D [N_dict, T])."""
-    D = dictionary(z, dr0, taps, taps, n_pupil, n_fft)
+    D = dictionary(z, dr0, taps, taps, n_pupil, n_fft, phase_scale=phase_scale)
     return svd_basis(D, K), D

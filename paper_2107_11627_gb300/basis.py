@@ -58,8 +58,11 @@ def _zernike_modes(js, n_pupil: int) -> np.ndarray:
 
 
 def psf_dictionary(n_dict: int, taps: int, n_pupil: int = 32, n_fft: int = 64, seed: int = 2021,
-                   dr0_range=(0.5, 6.0), chunk: int = 2000, with_alpha: bool = False):
-    """[n_dict, taps*taps] unit-sum PSFs (and, with_alpha, the [n_dict, 35] coefficients alpha_2..36)."""
+                   dr0_range=(0.5, 6.0), chunk: int = 2000, with_alpha: bool = False, phase_scale: float = 1.0):
+    """[n_dict, taps*taps] unit-sum PSFs (and, with_alpha, the [n_dict, 35] coefficients alpha_2..36).
+
+    phase_scale: the PSFs seen at another wavelength (phase alpha * phase_scale; pass the pupil
+    sample count of that wavelength as n_pupil, see build_basis_spectral)."""
     z, dr0 = inputs.dictionary_draws(n_dict, 35, dr0_range, seed)
     L = np.linalg.cholesky(p2s.noll_covariance(36))
     alpha = (dr0[:, None] ** (5.0 / 6.0)) * (z @ L.T)
@@ -69,7 +72,7 @@ def psf_dictionary(n_dict: int, taps: int, n_pupil: int = 32, n_fft: int = 64, s
     h0 = c - taps // 2
     rows = []
     for s0 in range(0, n_dict, chunk):
-        phi = (alpha[s0:s0 + chunk, 2:] @ Zf).reshape(-1, n_pupil, n_pupil)
+        phi = ((alpha[s0:s0 + chunk, 2:] * phase_scale) @ Zf).reshape(-1, n_pupil, n_pupil)
         pad = np.zeros((phi.shape[0], n_fft, n_fft), dtype=np.complex128)
         pad[:, :n_pupil, :n_pupil] = mask * np.exp(-1j * phi)
         h = np.fft.fftshift(np.abs(np.fft.fft2(pad)) ** 2, axes=(-2, -1))[:, h0:h0 + taps, h0:h0 + taps]
@@ -93,3 +96,29 @@ def build_basis(K: int = 100, taps: int = 33, n_dict: int = 50_000, n_pupil: int
         os.makedirs(_CACHE, exist_ok=True)
         np.save(path, H)
     return H
+
+
+def build_basis_spectral(K: int = 100, taps: int = 33, n_dict: int = 50_000, wavelengths_nm=(570.0, 540.0, 450.0),
+                         ref_nm: float = 540.0, n_pupil: int = 32, n_fft: int = 64, seed: int = 2021,
+                         cache: bool = True):
+    """Three [K, taps*taps] bases, one per colour channel (Sec. 3.5): the same draws seen at
+    wavelength lambda_c, i.e. the phase scaled by s_c = lambda_ref / lambda_c and the pupil
+    sampled with round(n_pupil s_c) samples across in the same n_fft DFT (the image pixel is
+    one angle at every wavelength, so the diffraction PSF widens with lambda)."""
+    out = []
+    for lam in wavelengths_nm:
+        s = ref_nm / lam
+        npc = int(round(n_pupil * s))
+        path = os.path.join(_CACHE, f"basis_K{K}_T{taps}_N{n_dict}_P{npc}_F{n_fft}_S{seed}_L{lam:g}_R{ref_nm:g}.npy")
+        if cache and os.path.exists(path):
+            out.append(np.load(path))
+            continue
+        D = psf_dictionary(n_dict, taps, npc, n_fft, seed, phase_scale=s)
+        _, _, vt = np.linalg.svd(D, full_matrices=False)
+        H = vt[:K].copy()
+        H[H.sum(axis=1) < 0] *= -1.0
+        if cache:
+            os.makedirs(_CACHE, exist_ok=True)
+            np.save(path, H)
+        out.append(H)
+    return out

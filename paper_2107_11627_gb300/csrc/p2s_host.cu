@@ -1056,6 +1056,55 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     return st;
 }
 
+p2s_status p2s_simulate_spectral(p2s_ctx *const *ctx3, const p2s_image *frames, int n, const float *d_over_r0,
+                                 const unsigned long long *seeds, const p2s_image *out, void *stream) {
+    if (!ctx3 || !ctx3[0] || !ctx3[1] || !ctx3[2]) return einval("ctx3 must hold three contexts");
+    const p2s_ctx *a = ctx3[0];
+    for (int c = 1; c < 3; ++c) {
+        const p2s_ctx *b = ctx3[c];
+        // one turbulence realisation: identical fields and warps in every channel
+        if (b->device != a->device || b->s != a->s || b->n_kernels != a->n_kernels || b->ell != a->ell ||
+            b->guard != a->guard || b->kappa != a->kappa || b->field_method != a->field_method ||
+            b->blur_then_warp != a->blur_then_warp)
+            return einval("the three contexts must share device, correlation parameters, kappa and options");
+    }
+    p2s_status st = validate_simulate(ctx3[0], frames, n, d_over_r0, seeds, out);
+    if (st != P2S_OK) return st;
+    for (int i = 0; i < n; ++i)
+        if (frames[i].C != 3) return einval("spectral frames are RGB (C = 3)");
+    if (n == 0) return P2S_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // per frame: an input plane and an output plane of H x W floats
+    size_t total = 0;
+    std::vector<size_t> off(n);
+    for (int i = 0; i < n; ++i) {
+        off[i] = total;
+        total += (((size_t)frames[i].H * frames[i].W * sizeof(float)) + 255) & ~(size_t)255;
+    }
+    char *buf = nullptr;
+    P2S_CUDA(cudaMallocAsync((void **)&buf, 2 * total, s));
+    std::vector<p2s_image> pin(n), pout(n);
+    for (int i = 0; i < n; ++i) {
+        pin[i] = p2s_image{(float *)(buf + off[i]), frames[i].H, frames[i].W, 1};
+        pout[i] = p2s_image{(float *)(buf + total + off[i]), frames[i].H, frames[i].W, 1};
+    }
+    for (int c = 0; c < 3 && st == P2S_OK; ++c) {
+        for (int i = 0; i < n && st == P2S_OK; ++i) {
+            const float *f_src[1] = {frames[i].data};
+            float *f_dst[1] = {pin[i].data};
+            st = launch_channel_copy(f_src, f_dst, 1, (long long)frames[i].H * frames[i].W, 3, c, 1, 0, s);
+        }
+        if (st == P2S_OK) st = p2s_simulate(ctx3[c], pin.data(), n, d_over_r0, seeds, pout.data(), stream);
+        for (int i = 0; i < n && st == P2S_OK; ++i) {
+            const float *f_src[1] = {pout[i].data};
+            float *f_dst[1] = {out[i].data};
+            st = launch_channel_copy(f_src, f_dst, 1, (long long)frames[i].H * frames[i].W, 1, 0, 3, c, s);
+        }
+    }
+    cudaFreeAsync(buf, s);
+    return st;
+}
+
 p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
                         const unsigned long long *seeds, const p2s_image *out, void *stream, int reps,
                         p2s_tune_result *res) {
@@ -1063,18 +1112,22 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     if (st != P2S_OK) return st;
     if (reps < 1) return einval("reps must be >= 1");
     const bool tc = ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16;  // FP8: one kernel, nothing to tune
-    int option = 0;
-    std::vector<int> cand;
+    int option = 0, option2 = 0;
+    std::vector<int> cand, cand2;
     if (tc && ctx->form == P2S_GATHER) {
         option = P2S_OPT_GATHER_SPLIT;
-        cand = {0, 1, 2, 3};
+        option2 = P2S_OPT_GATHER_BAND_ROWS;  // the fused kernel's tile height
+        cand = {1, 2, 3, 0, 0};
+        cand2 = {0, 0, 0, 32, 16};
     } else if (tc && ctx->form == P2S_SCATTER) {
         option = P2S_OPT_SCATTER_SEGMENT_ROWS;
-        cand = {32, 64, 128, 256, 1024};
+        cand = {8, 16, 32, 64, 128, 1024};
+        cand2.assign(cand.size(), 0);
     }
     p2s_tune_result r;
     std::memset(&r, 0, sizeof r);
     r.option = option;
+    r.option2 = option2;
     if (cand.empty()) {
         if (res) *res = r;
         return P2S_OK;
@@ -1086,6 +1139,7 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     float best = 1e30f;
     for (size_t c = 0; c < cand.size() && c < 8; ++c) {
         if ((st = p2s_set_option(ctx, option, cand[c])) != P2S_OK) break;
+        if (cand2[c] && (st = p2s_set_option(ctx, option2, cand2[c])) != P2S_OK) break;
         if ((st = p2s_simulate(ctx, frames, n, d_over_r0, seeds, out, stream)) != P2S_OK) break;
         cudaEventRecord(e0, s);
         for (int k = 0; k < reps && st == P2S_OK; ++k) st = p2s_simulate(ctx, frames, n, d_over_r0, seeds, out, stream);
@@ -1099,6 +1153,7 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         r.value[r.n] = cand[c];
+        r.value2[r.n] = cand2[c];
         r.ms[r.n] = ms / reps;
         if (r.ms[r.n] < best) {
             best = r.ms[r.n];
@@ -1110,6 +1165,7 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     cudaEventDestroy(e1);
     if (st != P2S_OK) return st;
     st = p2s_set_option(ctx, option, r.value[r.best]);
+    if (st == P2S_OK && r.value2[r.best]) st = p2s_set_option(ctx, option2, r.value2[r.best]);
     if (res) *res = r;
     return st;
 }

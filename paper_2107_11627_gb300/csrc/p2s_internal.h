@@ -36,6 +36,11 @@ struct FieldGeom {
     int Fh, Fw;  // torus (powers of two)
 };
 
+// Wavelength-dependent colour: copy one channel of n frames of npx pixels between
+// interleaved and planar layouts (strides and offsets in floats).
+p2s_status launch_channel_copy(const float *const *src, float *const *dst, int n, long long npx, int src_stride,
+                               int src_off, int dst_stride, int dst_off, cudaStream_t st);
+
 // Precisions that run the network and the contraction on the tensor cores.
 inline bool tc_precision(p2s_precision p) { return p == P2S_BF16 || p == P2S_FP16 || p == P2S_FP8E4M3; }
 

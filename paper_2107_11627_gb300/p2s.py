@@ -44,7 +44,8 @@ class p2s_kernel_stat(C.Structure):
 
 
 class p2s_tune_result(C.Structure):
-    _fields_ = [("option", C.c_int), ("n", C.c_int), ("value", C.c_int * 8), ("ms", C.c_float * 8), ("best", C.c_int)]
+    _fields_ = [("option", C.c_int), ("option2", C.c_int), ("n", C.c_int), ("value", C.c_int * 8),
+                ("value2", C.c_int * 8), ("ms", C.c_float * 8), ("best", C.c_int)]
 
 
 class p2s_server_config(C.Structure):
@@ -92,6 +93,8 @@ _SIGS = {
                                C.POINTER(p2s_tune_result)]),
     "p2s_get_option": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "p2s_stage_mlp16": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "p2s_simulate_spectral": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(p2s_image), C.c_int, C.POINTER(C.c_float),
+                                        C.POINTER(C.c_ulonglong), C.POINTER(p2s_image), C.c_void_p]),
     "p2s_contraction_scales": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float)]),
     "p2s_stage_blur": (C.c_int, [C.c_void_p, C.POINTER(p2s_image), C.c_void_p, C.POINTER(p2s_image), C.c_void_p]),
     "p2s_stage_mlp_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -251,8 +254,10 @@ class Simulator:
         return out
 
     def autotune(self, frames, d_over_r0, seeds, out=None, reps: int = 2, stream=None):
-        """Times the path's tile-shape candidates on this batch, keeps the fastest.
-        Returns {"option": name or None, "candidates": {value: ms}, "best": value}."""
+        """Times the path's kernel and tile-shape candidates on this batch, keeps the fastest.
+        Returns {"option": name or None, "option2": name or None, "candidates": {key: ms},
+        "best": key}, key = the option's value, or (value, value2) when a second option is tuned
+        with it (value2 0: that option left as it was)."""
         torch = _torch()
         frames = list(frames)
         n = len(frames)
@@ -266,8 +271,10 @@ class Simulator:
                                   sd.ctypes.data_as(C.POINTER(C.c_ulonglong)), oi, _stream_handle(stream), int(reps),
                                   C.byref(r)), "p2s_autotune")
         names = {v: k for k, v in self.OPTIONS.items()}
-        cands = {r.value[i]: float(r.ms[i]) for i in range(r.n)}
-        return {"option": names.get(r.option), "candidates": cands, "best": r.value[r.best] if r.n else None}
+        key = (lambda i: (r.value[i], r.value2[i])) if r.option2 else (lambda i: r.value[i])
+        cands = {key(i): float(r.ms[i]) for i in range(r.n)}
+        return {"option": names.get(r.option), "option2": names.get(r.option2), "candidates": cands,
+                "best": key(r.best) if r.n else None}
 
     def simulate_host(self, frames, d_over_r0, seeds, out=None, stream=None):
         """Host (NumPy float32) frames in and out; copies happen inside the call."""
@@ -354,6 +361,54 @@ class Simulator:
             raise ValueError("beta must be contiguous float32 [H, W, K]")
         _check(lib().p2s_stage_blur(self.ctx, C.byref(_image(xw)), C.c_void_p(beta.data_ptr()), C.byref(_image(out)),
                                     _stream_handle(stream)), "p2s_stage_blur")
+        return out
+
+
+class SpectralSimulator:
+    """Wavelength-dependent colour (p2s_simulate_spectral): three contexts, channel c with
+    basis bases[c] and the network's first layer scaled by lambda_ref / lambda_c (alpha is in
+    radians at the reference wavelength).  layers: one network for all channels or a list
+    of three.  Other arguments as Simulator (shared by the three contexts)."""
+
+    def __init__(self, bases, taps, layers, wavelengths_nm=(570.0, 540.0, 450.0), ref_nm: float = 540.0,
+                 **kwargs):
+        if len(bases) != 3 or len(wavelengths_nm) != 3:
+            raise ValueError("three bases and three wavelengths (R, G, B)")
+        per = isinstance(layers[0], list)
+        self.scales = [ref_nm / lam for lam in wavelengths_nm]
+        self.sims = []
+        for c in range(3):
+            lay = layers[c] if per else layers
+            W1, b1 = lay[0]
+            lay_c = [(np.asarray(W1, dtype=np.float64) * self.scales[c], b1)] + list(lay[1:])
+            self.sims.append(Simulator(bases[c], taps, lay_c, **kwargs))
+
+    def close(self):
+        for sm in self.sims:
+            sm.close()
+
+    def set_option(self, name: str, value: int):
+        for sm in self.sims:
+            sm.set_option(name, value)
+
+    def check(self, stream=None):
+        for sm in self.sims:
+            sm.check(stream)
+
+    def simulate(self, frames, d_over_r0, seeds, out=None, stream=None):
+        """frames: list of CUDA tensors [H, W, 3]; returns the outputs."""
+        torch = _torch()
+        frames = list(frames)
+        n = len(frames)
+        if out is None:
+            out = [torch.empty_like(f) for f in frames]
+        dr, sd = Simulator._meta(d_over_r0, seeds, n)
+        fi = (p2s_image * max(n, 1))(*[_image(f) for f in frames])
+        oi = (p2s_image * max(n, 1))(*[_image(o) for o in out])
+        ctxs = (C.c_void_p * 3)(*[sm.ctx for sm in self.sims])
+        _check(lib().p2s_simulate_spectral(ctxs, fi, n, dr.ctypes.data_as(C.POINTER(C.c_float)),
+                                           sd.ctypes.data_as(C.POINTER(C.c_ulonglong)), oi, _stream_handle(stream)),
+               "p2s_simulate_spectral")
         return out
 
 

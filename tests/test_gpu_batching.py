@@ -130,8 +130,15 @@ def test_autotune_picks_a_candidate_and_keeps_results(form):
     before = sim.simulate(xs, [2.0, 4.0], [3, 4])
     r = sim.autotune(xs, [2.0, 4.0], [3, 4], reps=1)
     assert r["option"] == ("gather_split" if form == "gather" else "scatter_segment_rows")
-    assert len(r["candidates"]) >= 2 and r["best"] in r["candidates"]
-    assert sim.get_option(r["option"]) == r["best"]
+    assert len(r["candidates"]) >= 5 and r["best"] in r["candidates"]
+    if form == "gather":
+        assert r["option2"] == "gather_band_rows"
+        assert set(r["candidates"]) == {(1, 0), (2, 0), (3, 0), (0, 32), (0, 16)}
+        assert sim.get_option(r["option"]) == r["best"][0]
+        if r["best"][1]:
+            assert sim.get_option(r["option2"]) == r["best"][1]
+    else:
+        assert sim.get_option(r["option"]) == r["best"]
     after = sim.simulate(xs, [2.0, 4.0], [3, 4])
     sim.check()
     # fused and split gather kernels differ by the FP16 rounding of G in the split
