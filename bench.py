@@ -38,8 +38,9 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # x_w exceeding L2 already at 8 frames).  Each figure holds for the kernel source it was measured
 # on (sha1 prefix of the file); a changed source reports traffic null until it is measured again.
 TRAFFIC = {
-    "blur_tc_gather16": {"bytes_per_frame": (495875840 + 24105216) / 8, "source": "k_gather.cu", "sha1": "f23e6222e865"},
-    "net_tc": {"bytes_per_frame": (5707008 + 408403712) / 8, "source": "k_net.cu", "sha1": "86d4e4205d07"},
+    "blur_tc_gather16": {"bytes_per_frame": (496030976 + 20580352) / 8, "source": "k_gather.cu", "sha1": "52a4511d7d65"},
+    "net_tc": {"bytes_per_frame": (5684480 + 405020416) / 8, "source": "k_net.cu", "sha1": "68fa7cb337fd"},
+    "blur_tc_scatter": {"bytes_per_frame": (505922560 + 21190912) / 8, "source": "k_scatter.cu", "sha1": "143651bfc23e"},
 }
 # the blur kernels: tensor flops 2 K T per pixel (the contraction; the fused kernel adds the
 # network's), tap accumulation 2 C T FP32 flops per pixel on the FMA pipe

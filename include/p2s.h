@@ -122,7 +122,11 @@ typedef struct {
  * factor in FP64 (Sec. 2.2), and the field filter tables.  Runs on the
  * current CUDA device.  Errors: EINVAL on inconsistent shapes (dims[0] != 33,
  * dims[last] != K, even taps, spacing < 1, n_kernels not 1 or 7); ENOMEM;
- * EUNSUPPORTED if the (precision, form) pair is not built for this device. */
+ * EUNSUPPORTED if the (precision, form) pair is not built for this device.
+ * Limits: K <= 128, taps <= 33 x 33 and network widths <= 128 on every path;
+ * the tensor-core paths (FP16, BF16, FP8) need exactly 33 x 33 taps, three
+ * layers and K <= 110; FP8 E4M3 runs the gather form only
+ * and the FFT form FP32 only. */
 p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr_params *corr,
                       p2s_precision precision, p2s_blur_form form, p2s_ctx **out);
 

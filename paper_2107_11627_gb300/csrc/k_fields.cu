@@ -185,6 +185,191 @@ __global__ void __launch_bounds__(kThreads) col_filter_kernel(int Fh, int Ah, in
     }
 }
 
+// ---- one kernel per field: both filter passes with warp-register FFTs ----------
+//
+// A warp transforms one complex sequence of N = 32 P points, lane l holding
+// elements l + 32 i (i < P): a P-point DFT in the thread, the twiddle
+// w_N^(l k1), then a 32-point DFT across the lanes by five radix-2 shuffle
+// stages (decimation in frequency), which leaves X[k1 + P bitrev5(l)] in lane l,
+// register k1.  The gain is real, so the spectrum is multiplied in that order
+// and the inverse runs the same steps backwards (decimation in time from
+// bit-reversed input), ending in natural order: no reordering pass at all.
+// tw[m] = exp(-2 pi i m / N) for m < N / 2 (shared memory), w^(m + N/2) = -w^m.
+
+__device__ __forceinline__ float2 tw_at(const float2 *tw, int m, int N, bool inverse) {
+    float2 w = tw[m & (N / 2 - 1)];
+    if (m & (N / 2)) w = make_float2(-w.x, -w.y);
+    if (inverse) w.y = -w.y;
+    return w;
+}
+
+// v[i] <- sum_k v[k] w_P^(i k) (w_P = exp(-+2 pi i / P)), P a power of two, by an iterative
+// radix-2 decimation in time on the bit-reversed order; N is the table's length.
+template <int P>
+__device__ __forceinline__ void dft_in_thread(float2 (&v)[P], const float2 *tw, int N, bool inverse) {
+    if constexpr (P == 1) return;
+    float2 a[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        int r = 0;
+#pragma unroll
+        for (int b = 1; b < P; b <<= 1) r = (r << 1) | ((i / b) & 1);
+        a[r] = v[i];
+    }
+#pragma unroll
+    for (int len = 2; len <= P; len <<= 1)
+#pragma unroll
+        for (int i0 = 0; i0 < P; i0 += len)
+#pragma unroll
+            for (int j = 0; j < len / 2; ++j) {
+                const float2 w = tw_at(tw, j * (N / len), N, inverse);
+                const float2 x0 = a[i0 + j], x1 = cmul(a[i0 + j + len / 2], w);
+                a[i0 + j] = make_float2(x0.x + x1.x, x0.y + x1.y);
+                a[i0 + j + len / 2] = make_float2(x0.x - x1.x, x0.y - x1.y);
+            }
+#pragma unroll
+    for (int i = 0; i < P; ++i) v[i] = a[i];
+}
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+template <int P>
+__device__ __forceinline__ void warp_fft_fwd(float2 (&v)[P], const float2 *tw, int lane) {
+    constexpr int N = 32 * P;
+    dft_in_thread<P>(v, tw, N, false);
+#pragma unroll
+    for (int k1 = 1; k1 < P; ++k1) v[k1] = cmul(v[k1], tw_at(tw, lane * k1, N, false));
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool hi = lane & h;
+        const float2 w = tw_at(tw, (lane & (h - 1)) * (N / (2 * h)), N, false);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            const float2 o = shfl_xor2(v[k1], h);
+            v[k1] = hi ? cmul(make_float2(o.x - v[k1].x, o.y - v[k1].y), w)
+                       : make_float2(v[k1].x + o.x, v[k1].y + o.y);
+        }
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void warp_fft_inv(float2 (&v)[P], const float2 *tw, int lane) {
+    constexpr int N = 32 * P;
+#pragma unroll
+    for (int h = 1; h <= 16; h <<= 1) {
+        const bool hi = lane & h;
+        const float2 w = tw_at(tw, (lane & (h - 1)) * (N / (2 * h)), N, true);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            const float2 o = shfl_xor2(v[k1], h);
+            if (hi) {
+                const float2 t = cmul(v[k1], w);
+                v[k1] = make_float2(o.x - t.x, o.y - t.y);
+            } else {
+                const float2 t = cmul(o, w);
+                v[k1] = make_float2(v[k1].x + t.x, v[k1].y + t.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < P; ++k1) v[k1] = cmul(v[k1], tw_at(tw, lane * k1, N, true));
+    dft_in_thread<P>(v, tw, N, true);
+}
+
+__device__ __forceinline__ int bitrev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
+
+constexpr int kFieldWarps = 8;
+
+// Row pass (white noise rows (2 r, 2 r + 1) packed as one complex row, filtered along x,
+// columns [0, Aw) kept in shared memory), then column pass (columns (2 c, 2 c + 1) of that
+// block filtered along y, rows [0, Ah) to f[frame][mode][y][x]).  One CTA per (mode, frame);
+// the same arithmetic as row_filter_kernel and col_filter_kernel.
+template <int PW, int PH>
+__global__ void __launch_bounds__(32 * kFieldWarps, 1) field_kernel(FrameBatch fb, int Ah, int Aw, int pitch,
+                                                                  const float2 *__restrict__ twx,
+                                                                  const float *__restrict__ gainx,
+                                                                  const float2 *__restrict__ twy,
+                                                                  const float *__restrict__ gainy,
+                                                                  const int *__restrict__ kernel_of_mode, float *f) {
+    constexpr int Fw = 32 * PW, Fh = 32 * PH;
+    extern __shared__ float sfm[];
+    float *tb = sfm;                                   // [Fh][pitch]: the row pass's columns < Aw
+    float *stage = tb + Fh * pitch;                    // [warps][2 Fw]: a row pair of white noise
+    float *gx = stage + kFieldWarps * 2 * Fw, *gy = gx + Fw;
+    float2 *tx = (float2 *)(gy + Fh), *ty = tx + Fw / 2;
+    const int mode = blockIdx.x, frame = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kk = kernel_of_mode[mode];
+    for (int i = threadIdx.x; i < Fw; i += blockDim.x) gx[i] = gainx[(size_t)kk * Fw + i];
+    for (int i = threadIdx.x; i < Fh; i += blockDim.x) gy[i] = gainy[(size_t)kk * Fh + i];
+    for (int i = threadIdx.x; i < Fw / 2; i += blockDim.x) tx[i] = twx[i];
+    for (int i = threadIdx.x; i < Fh / 2; i += blockDim.x) ty[i] = twy[i];
+    __syncthreads();
+    const unsigned long long seed = fb.seed[frame];
+    float *st = stage + warp * 2 * Fw;
+    for (int rp = warp; rp < Fh / 2; rp += kFieldWarps) {
+        // noise: samples [2 rp Fw, (2 rp + 2) Fw) of stream (seed, mode), quad by quad
+        const uint32_t q0 = (uint32_t)(2 * rp * Fw) >> 2;
+        for (int qq = lane; qq < Fw / 2; qq += 32) {
+            float z[4];
+            normals4(seed, mode, q0 + qq, z);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) st[4 * qq + i] = z[i];
+        }
+        __syncwarp();
+        float2 v[PW];
+#pragma unroll
+        for (int i = 0; i < PW; ++i) v[i] = make_float2(st[lane + 32 * i], st[Fw + lane + 32 * i]);
+        __syncwarp();
+        warp_fft_fwd<PW>(v, tx, lane);
+        const int kb = PW * bitrev5(lane);
+#pragma unroll
+        for (int k1 = 0; k1 < PW; ++k1) {
+            const float g = gx[k1 + kb];
+            v[k1] = make_float2(v[k1].x * g, v[k1].y * g);
+        }
+        warp_fft_inv<PW>(v, tx, lane);
+#pragma unroll
+        for (int i = 0; i < PW; ++i) {
+            const int x = lane + 32 * i;
+            if (x < Aw) {
+                tb[(2 * rp) * pitch + x] = v[i].x;
+                tb[(2 * rp + 1) * pitch + x] = v[i].y;
+            }
+        }
+    }
+    __syncthreads();
+    float *ff = f + ((size_t)frame * kModes + mode) * Ah * Aw;
+    for (int cp = warp; 2 * cp < Aw; cp += kFieldWarps) {
+        const int x0 = 2 * cp;
+        const bool two = x0 + 1 < Aw;
+        float2 v[PH];
+#pragma unroll
+        for (int i = 0; i < PH; ++i) {
+            const int y = lane + 32 * i;
+            v[i] = make_float2(tb[y * pitch + x0], two ? tb[y * pitch + x0 + 1] : 0.0f);
+        }
+        warp_fft_fwd<PH>(v, ty, lane);
+        const int kb = PH * bitrev5(lane);
+#pragma unroll
+        for (int k1 = 0; k1 < PH; ++k1) {
+            const float g = gy[k1 + kb];
+            v[k1] = make_float2(v[k1].x * g, v[k1].y * g);
+        }
+        warp_fft_inv<PH>(v, ty, lane);
+#pragma unroll
+        for (int i = 0; i < PH; ++i) {
+            const int y = lane + 32 * i;
+            if (y < Ah) {
+                ff[(size_t)y * Aw + x0] = v[i].x;
+                if (two) ff[(size_t)y * Aw + x0 + 1] = v[i].y;
+            }
+        }
+    }
+}
+
 // alpha(a) = (D/r0)^(5/6) L f(a): slot 0 (piston) = 0, slot l+1 = mode l + 2.
 __global__ void colour_kernel(FrameBatch fb, int A, const float *__restrict__ L, const float *__restrict__ f,
                               float *alpha) {
@@ -218,6 +403,40 @@ p2s_status launch_noise(unsigned long long seed, int mode, int Fh, int Fw, float
     noise_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, st>>>(seed, mode, n, out);
     P2S_CUDA(cudaGetLastError());
     return P2S_OK;
+}
+
+// The one-kernel filter for tori of 32 .. 256 points per axis whose row-pass block fits
+// in shared memory; false: use the two-pass kernels.
+template <int PW, int PH>
+static p2s_status launch_field_pw_ph(const FieldGeom &g, const FrameBatch &fb, int pitch, size_t smem,
+                                     const FilterTable *tw, const FilterTable *th, const int *kom, float *f,
+                                     cudaStream_t st) {
+    P2S_CUDA(cudaFuncSetAttribute(field_kernel<PW, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    field_kernel<PW, PH><<<dim3(kModes, fb.n), 32 * kFieldWarps, smem, st>>>(fb, g.Ah, g.Aw, pitch, tw->twiddle,
+                                                                             tw->gain, th->twiddle, th->gain, kom, f);
+    P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+template <int PW>
+static p2s_status launch_field_pw(int PH, const FieldGeom &g, const FrameBatch &fb, int pitch, size_t smem,
+                                  const FilterTable *tw, const FilterTable *th, const int *kom, float *f,
+                                  cudaStream_t st) {
+    switch (PH) {
+        case 1: return launch_field_pw_ph<PW, 1>(g, fb, pitch, smem, tw, th, kom, f, st);
+        case 2: return launch_field_pw_ph<PW, 2>(g, fb, pitch, smem, tw, th, kom, f, st);
+        case 4: return launch_field_pw_ph<PW, 4>(g, fb, pitch, smem, tw, th, kom, f, st);
+        default: return launch_field_pw_ph<PW, 8>(g, fb, pitch, smem, tw, th, kom, f, st);
+    }
+}
+
+static bool field_kernel_fits(const FieldGeom &g, int *pitch, size_t *smem) {
+    auto ok_len = [](int F) { return F == 32 || F == 64 || F == 128 || F == 256; };
+    if (!ok_len(g.Fw) || !ok_len(g.Fh) || g.Aw > g.Fw || g.Ah > g.Fh) return false;
+    *pitch = g.Aw | 1;  // odd: the column pass reads 32 rows of one column without bank conflicts
+    *smem = ((size_t)g.Fh * *pitch + (size_t)kFieldWarps * 2 * g.Fw + g.Fw + g.Fh) * sizeof(float) +
+            (size_t)(g.Fw / 2 + g.Fh / 2) * sizeof(float2);
+    return *smem <= 160 * 1024;
 }
 
 size_t fields_scratch_bytes(const FieldGeom &g, int n) {
@@ -355,6 +574,27 @@ p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb,
     float *t = (float *)scratch;
     const size_t t_bytes = (size_t)fb.n * kModes * g.Fh * g.Aw * sizeof(float);
     float *f = (float *)((char *)scratch + ((t_bytes + 255) & ~(size_t)255));
+    int pitch = 0;
+    size_t fsmem = 0;
+    if (field_kernel_fits(g, &pitch, &fsmem)) {
+        ProfScope pf(ctx, st, "fields_filter", 0.0, (double)fb.n * kModes * g.Ah * g.Aw * 4);
+        const int PW = g.Fw / 32, PH = g.Fh / 32;
+        p2s_status rs;
+        switch (PW) {
+            case 1: rs = launch_field_pw<1>(PH, g, fb, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, f, st); break;
+            case 2: rs = launch_field_pw<2>(PH, g, fb, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, f, st); break;
+            case 4: rs = launch_field_pw<4>(PH, g, fb, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, f, st); break;
+            default: rs = launch_field_pw<8>(PH, g, fb, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, f, st); break;
+        }
+        if (rs != P2S_OK) return rs;
+        const int A = g.Ah * g.Aw;
+        dim3 grid_a((A + 127) / 128, fb.n);
+        ProfScope pa(ctx, st, "fields_colour", (double)fb.n * A * kModes * (kModes + 1),
+                     (double)fb.n * A * (kModes + kAlphaStride) * 4);
+        colour_kernel<<<grid_a, 128, 0, st>>>(fb, A, ctx->d_L, f, alpha);
+        P2S_CUDA(cudaGetLastError());
+        return P2S_OK;
+    }
 
     // rows: R row pairs per CTA, R * Fw <= kFftElems
     int R = kFftElems / g.Fw;

@@ -16,7 +16,8 @@
 //             FP16 RGB in 8 bytes, widened to FP32 on load: 2/3 of the FP32
 //             staging traffic, the contraction's largest shared-memory stream),
 //             accumulates in FP32.
-// Roles: warp 0 issues MMAs (one thread), warp 1 streams weights and basis
+// Roles: warps 0 and 10 issue MMAs (one thread each, one output row each: a
+// single issuing thread caps tcgen05.mma at one per ~76 cycles), warp 1 streams weights and basis
 // chunks into a 3-slot shared-memory ring with 1-D bulk copies, warps 2..9
 // (two per TMEM lane quadrant) convert between layers and run the gather;
 // the two halves take alternate chunks, each with its own TMEM buffer.
