@@ -39,12 +39,14 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # on (sha1 prefix of the file); a changed source reports traffic null until it is measured again.
 TRAFFIC = {
     "blur_tc_gather16": {"bytes_per_frame": (496030976 + 20580352) / 8, "source": "k_gather.cu", "sha1": "52a4511d7d65"},
+    "blur_tc_gather_h2": {"bytes_per_frame": (501768192 + 20147968) / 8, "source": "k_gather_h2.cu", "sha1": "f56ebc317ed4"},
     "net_tc": {"bytes_per_frame": (5684480 + 405020416) / 8, "source": "k_net.cu", "sha1": "68fa7cb337fd"},
     "blur_tc_scatter": {"bytes_per_frame": (505922560 + 21190912) / 8, "source": "k_scatter.cu", "sha1": "143651bfc23e"},
 }
 # the blur kernels: tensor flops 2 K T per pixel (the contraction; the fused kernel adds the
 # network's), tap accumulation 2 C T FP32 flops per pixel on the FMA pipe
-BLUR_KERNELS = ("blur_tc_gather16", "blur_tc_gather16f", "blur_tc_gather_x32", "fused_tc_gather", "blur_tc_scatter")
+BLUR_KERNELS = ("blur_tc_gather16", "blur_tc_gather_h2", "blur_tc_gather8", "blur_tc_gather16f", "blur_tc_gather_x32",
+                "fused_tc_gather", "blur_tc_scatter")
 
 
 def source_sha1(name: str) -> str:

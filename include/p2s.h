@@ -269,14 +269,23 @@ p2s_status p2s_selftest_stall(p2s_ctx *ctx, void *stream);
  *       L_y W L_x^T (at most 128 anchors per axis).
  *   P2S_OPT_GATHER_SPLIT  tensor-core gather form only.  0: one fused
  *       kernel evaluates the network and the blur per tile, beta never leaves
- *       the SM.  1 (default): the network kernel writes beta in its 16-bit
+ *       the SM.  1 (default in BF16 and FP8 contexts; the only value FP8
+ *       takes): the network kernel writes beta in its 16-bit
  *       operand layout (224 B per pixel of scratch) and a blur-only
  *       tensor-core kernel with four accumulating warps per TMEM lane
- *       quadrant reads it back.
- *       Rounding points of the fused kernel (beta and H in 16 bits, x staged
- *       in FP16, FP32 accumulation) plus one: G = beta H is rounded to FP16
- *       before the tap products (FP16 x FP16, exact in FP32), at most 2^-11
- *       relative per tap product.  A G beyond the FP16 range (|G| > 65504)
+ *       quadrant reads it back.  2, 3: the same split with one of two
+ *       fragment kernels (G read as 16x256b TMEM fragments; beta written with
+ *       its columns permuted within 32-column blocks; 3 keeps x and G in
+ *       FP32).  4: the same split with the tap products as packed FP16 FMAs
+ *       (two output rows per instruction; default in FP16 contexts), FP16
+ *       partial sums of 12 products
+ *       flushed into FP32 per basis chunk: 1e-4 to 1e-3 relative error on top
+ *       of kernel 1's, the more the PSF weights cancel (FP16 and BF16
+ *       contexts; not FP8).
+ *       Rounding points of kernel 1 (and 2): those of the fused kernel (beta
+ *       and H in 16 bits, x staged in FP16, FP32 accumulation) plus one:
+ *       G = beta H is rounded to FP16 before the tap products (FP16 x FP16,
+ *       exact in FP32), at most 2^-11 relative per tap product.  A G beyond the FP16 range (|G| > 65504)
  *       would overflow; PSF weights of the model are orders of magnitude
  *       smaller (the PSF taps sum to about 1), so this needs beta far outside
  *       anything the network produces, e.g. hand-made beta given to
@@ -300,7 +309,7 @@ p2s_status p2s_get_option(const p2s_ctx *ctx, int option, int *value);
  * calls with CUDA events on `stream` (synchronising it), keeps the fastest
  * setting in the context and reports every candidate in `res` (may be NULL).
  * Candidates: FP16 / BF16 tensor-core gather, the kernel and its tile shape
- * (P2S_OPT_GATHER_SPLIT 1, 2, 3 -- the three blur-only kernels, 128 x 32 and
+ * (P2S_OPT_GATHER_SPLIT 1 .. 4 -- the four blur-only kernels, 128 x 32 and
  * 128 x 16 tiles, one or four output columns per accumulating thread -- and 0,
  * the fused kernel, with P2S_OPT_GATHER_BAND_ROWS 16 or 32); tensor-core
  * scatter, P2S_OPT_SCATTER_SEGMENT_ROWS 8 .. 1024 (the rows per work unit);

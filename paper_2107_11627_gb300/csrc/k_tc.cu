@@ -835,6 +835,20 @@ p2s_status tc_prepare(p2s_ctx *ctx) {
         const int tx = 24 * (B / 3) + 6 * j + 2 * (B % 3) + e;
         return tx < kTaps ? basis_row(k, (kTaps - 1) * kTaps + tx) : (uint16_t)0;
     });
+    // The packed-FP16 gather kernel (k_gather_h2.cu): tap-row-major chunks whose second
+    // output row reads the image one tap row (32 N-rows) further in.
+    //   main chunk c: N-row n -> tap row 3 c + n / 32 - 1 (zero outside 0 .. 32), tap column n % 32
+    //   last chunk:   n < 32 -> tap row 32, tap column n; n < 65 -> tap row n - 32, tap column 32
+    for (int c = 0; c < kMainChunks; ++c)
+        add_image(128, kKP, [&](int n, int k) {
+            const int ty = 3 * c + n / 32 - 1, tx = n % 32;
+            return (ty >= 0 && ty < kTaps) ? basis_row(k, ty * kTaps + tx) : (uint16_t)0;
+        });
+    add_image(80, kKP, [&](int n, int k) {
+        if (n < 32) return basis_row(k, (kTaps - 1) * kTaps + n);
+        if (n < 32 + kTaps) return basis_row(k, (n - 32) * kTaps + kTaps - 1);
+        return (uint16_t)0;
+    });
     std::vector<float> bias(h1p + h2p, 0.f);
     for (int o = 0; o < ctx->dims[1]; ++o) bias[o] = (float)ctx->b[0][o];
     for (int o = 0; o < ctx->dims[2]; ++o) bias[h1p + o] = (float)ctx->b[1][o];

@@ -244,6 +244,8 @@ p2s_status p2s_create(const p2s_basis *basis, const p2s_mlp *mlp, const p2s_corr
     }
     ctx->prec = precision;
     ctx->form = form;
+    // default blur-only gather kernel: packed FP16 products for FP16 operands, kernel 1 otherwise
+    ctx->gather_split = precision == P2S_FP16 ? 4 : 1;
     ctx->K = basis->K;
     ctx->th = basis->taps_h;
     ctx->tw = basis->taps_w;
@@ -552,8 +554,8 @@ p2s_status p2s_set_option(p2s_ctx *ctx, int option, int value) {
         return P2S_OK;
     }
     if (option == P2S_OPT_GATHER_SPLIT) {
-        if (value < 0 || value > 3)
-            return einval("gather split is 0 (fused) or 1, 2, 3 (network, then one of three blur kernels)");
+        if (value < 0 || value > 4)
+            return einval("gather split is 0 (fused) or 1 .. 4 (network, then one of four blur kernels)");
         if (ctx->prec == P2S_FP8E4M3 && value != 1) {
             set_error("the FP8 E4M3 contraction runs in the split gather kernel 1 only");
             return P2S_EUNSUPPORTED;
@@ -665,14 +667,11 @@ p2s_status p2s_stage_blur(p2s_ctx *ctx, const p2s_image *xw, const float *beta, 
             // entries 0, so the folded bias rows add nothing: beta here includes the bias)
             cudaStream_t s = (cudaStream_t)stream;
             void *b16 = nullptr;
-            const int perm = ctx->gather_split >= 2 ? 1 : 0;
+            const int perm = gather_perm(ctx->gather_split);
             P2S_CUDA(cudaMallocAsync(&b16, beta16_bytes(xw->H, xw->W, 1, perm), s));
             st = launch_pack16(ctx, xw->H, xw->W, 1, beta, b16, perm, s);
             const void *bp[1] = {b16};
-            if (st == P2S_OK)
-                st = ctx->gather_split == 3 ? launch_gather_x32(ctx, &f, bp, 1, xw->C, ctx->d_status, s)
-                     : perm                  ? launch_gather_frag(ctx, &f, bp, 1, xw->C, ctx->d_status, s)
-                                             : launch_gather_split(ctx, &f, bp, 1, xw->C, ctx->d_status, s);
+            if (st == P2S_OK) st = launch_gather_blur(ctx, ctx->gather_split, &f, bp, 1, xw->C, ctx->d_status, s);
             cudaFreeAsync(b16, s);
             return st;
         }
@@ -818,7 +817,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
     std::vector<TcFrame> tf[2];      // C = 1, C = 3
     std::vector<const void *> b16[2];  // split form: each frame's beta16
     const bool split = ctx->gather_split != 0;
-    const int perm = ctx->gather_split >= 2 ? 1 : 0;  // the fragment kernels' beta layout
+    const int perm = gather_perm(ctx->gather_split);  // the fragment kernels' beta layout
     const bool f8 = ctx->prec == P2S_FP8E4M3;          // split kernel 1 with the FP8 layout
     struct PostWarp {
         FieldGeom g;
@@ -888,10 +887,8 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
     for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
         if (tf[ci].empty()) continue;
         const int C = ci ? 3 : 1;
-        st = ctx->gather_split == 3
-                 ? launch_gather_x32(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
-             : perm  ? launch_gather_frag(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
-             : split ? launch_gather_split(ctx, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C, ctx->d_status, s)
+        st = split ? launch_gather_blur(ctx, ctx->gather_split, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C,
+                                        ctx->d_status, s)
                    : launch_tc(ctx, kTcFull, tf[ci].data(), (int)tf[ci].size(), C, nullptr, nullptr, ctx->d_status, s);
     }
     for (const PostWarp &w : post_warp) {
@@ -1117,8 +1114,8 @@ p2s_status p2s_autotune(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
     if (tc && ctx->form == P2S_GATHER) {
         option = P2S_OPT_GATHER_SPLIT;
         option2 = P2S_OPT_GATHER_BAND_ROWS;  // the fused kernel's tile height
-        cand = {1, 2, 3, 0, 0};
-        cand2 = {0, 0, 0, 32, 16};
+        cand = {1, 2, 3, 4, 0, 0};
+        cand2 = {0, 0, 0, 0, 32, 16};
     } else if (tc && ctx->form == P2S_SCATTER) {
         option = P2S_OPT_SCATTER_SEGMENT_ROWS;
         cand = {8, 16, 32, 64, 128, 1024};

@@ -206,6 +206,22 @@ p2s_status launch_gather_frag(p2s_ctx *ctx, const TcFrame *frames, const void *c
 // The FP32-x variant (P2S_OPT_GATHER_SPLIT = 3): same beta layout, 128 x 16 tiles.
 p2s_status launch_gather_x32(p2s_ctx *ctx, const TcFrame *frames, const void *const *beta16, int n, int C,
                              int *status, cudaStream_t st);
+// The packed-FP16 variant (P2S_OPT_GATHER_SPLIT = 4): kernel 1's beta layout (perm = 0).
+p2s_status launch_gather_h2(p2s_ctx *ctx, const TcFrame *frames, const void *const *beta16, int n, int C,
+                            int *status, cudaStream_t st);
+// beta16 layout of the blur-only gather kernel `split` selects: the fragment kernels
+// (2, 3) read the permuted layout, kernels 1 and 4 the plain one
+inline int gather_perm(int split) { return (split == 2 || split == 3) ? 1 : 0; }
+// the blur-only gather kernel `split` (1 .. 4) over n frames
+inline p2s_status launch_gather_blur(p2s_ctx *ctx, int split, const TcFrame *frames, const void *const *beta16,
+                                     int n, int C, int *status, cudaStream_t st) {
+    switch (split) {
+        case 2: return launch_gather_frag(ctx, frames, beta16, n, C, status, st);
+        case 3: return launch_gather_x32(ctx, frames, beta16, n, C, status, st);
+        case 4: return launch_gather_h2(ctx, frames, beta16, n, C, status, st);
+        default: return launch_gather_split(ctx, frames, beta16, n, C, status, st);
+    }
+}
 p2s_status launch_tc(p2s_ctx *ctx, int mode, const TcFrame *frames, int n, int C, const float *beta_in,
                      float *beta_out, int *status, cudaStream_t st);
 constexpr int kTcFull = 0, kTcMlpOnly = 1, kTcBlurOnly = 2;

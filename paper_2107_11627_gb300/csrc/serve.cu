@@ -84,7 +84,7 @@ size_t footprint(const p2s_ctx *ctx, const p2s::FieldGeom &g, int C) {
     if (ctx->prec == P2S_FP8E4M3)
         b += p2s::beta8_bytes(g.H, g.W, 1);
     else if ((ctx->prec == P2S_BF16 || ctx->prec == P2S_FP16) && (ctx->form == P2S_SCATTER || ctx->gather_split))
-        b += p2s::beta16_bytes(g.H, g.W, 1, (ctx->form != P2S_SCATTER && ctx->gather_split >= 2) ? 1 : 0);
+        b += p2s::beta16_bytes(g.H, g.W, 1, (ctx->form != P2S_SCATTER) ? p2s::gather_perm(ctx->gather_split) : 0);
     else if (!p2s::tc_precision(ctx->prec))
         b += px * ctx->K * sizeof(float);
     return b + 4 * 1024;

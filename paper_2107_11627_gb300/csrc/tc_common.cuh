@@ -84,6 +84,28 @@ __device__ __forceinline__ void fma_mix_x1(uint32_t x, uint32_t gw, float &c) {
             : "+f"(c) : "r"(x), "r"(gw));
 }
 
+// a += g * (x, x) as one packed FP16 FMA, x the low (XHI false) or high half of the
+// word `x`: both halves of `a` accumulate in FP16, each rounded once per FMA.
+template <bool XHI>
+__device__ __forceinline__ void hfma2_bcast(uint32_t &a, uint32_t g, uint32_t x) {
+    if (XHI)
+        asm("{\n.reg .b16 xl, xh;\n.reg .b32 xb;\nmov.b32 {xl, xh}, %2;\nmov.b32 xb, {xh, xh};\n"
+            "fma.rn.f16x2 %0, %1, xb, %0;\n}\n"
+            : "+r"(a) : "r"(g), "r"(x));
+    else
+        asm("{\n.reg .b16 xl, xh;\n.reg .b32 xb;\nmov.b32 {xl, xh}, %2;\nmov.b32 xb, {xl, xl};\n"
+            "fma.rn.f16x2 %0, %1, xb, %0;\n}\n"
+            : "+r"(a) : "r"(g), "r"(x));
+}
+
+// c0 += lo(a), c1 += hi(a): an FP16 pair added into two FP32 sums (each an exact
+// product by 1.0 and one FP32 rounding, i.e. a plain FP32 add)
+__device__ __forceinline__ void flush_f16x2(uint32_t a, float &c0, float &c1) {
+    asm("{\n.reg .b16 al, ah, one;\nmov.b32 {al, ah}, %2;\nmov.b16 one, 0x3C00;\n"
+        "fma.rn.f32.f16 %0, al, one, %0;\nfma.rn.f32.f16 %1, ah, one, %1;\n}\n"
+        : "+f"(c0), "+f"(c1) : "r"(a));
+}
+
 // v0, v1 (FP32) as E4M3 hi/lo pairs: hi = e4m3(v), lo = e4m3(v - hi) (the difference is
 // exact in FP32), both rounded to nearest even and saturated at +-448.  Each result is
 // two bytes: v0's in the low byte, v1's in the high byte.
@@ -103,14 +125,15 @@ struct Ctl {
 // Bounded wait (about 2 s at 2 GHz); on timeout flags the CTA and the status
 // word.  Once the CTA is flagged every wait returns false at once, so all
 // roles run their (data-independent) loops to the end and meet at teardown.
+// Each try may suspend the thread for up to 20 us (it resumes when the phase
+// completes), so a waiting thread takes no issue slots from working warps.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, const Ctl &ctl, int code,
                                          long long limit = 4000000000ll) {
     if (ptx::mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
-    for (int spins = 0;; ++spins) {
-        if (ptx::mbar_try(bar, parity)) return true;
+    for (;;) {
+        if (ptx::mbar_try_hint(bar, parity, 20000u)) return true;
         if (*ctl.abort) return false;
-        if (spins > 4) __nanosleep(spins < 64 ? 32 : 128);  // leave issue slots to working warps
         if (clock64() - t0 > limit) {
             *ctl.abort = 1;
             atomicOr(ctl.status, code);

@@ -133,7 +133,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(form):
     assert len(r["candidates"]) >= 5 and r["best"] in r["candidates"]
     if form == "gather":
         assert r["option2"] == "gather_band_rows"
-        assert set(r["candidates"]) == {(1, 0), (2, 0), (3, 0), (0, 32), (0, 16)}
+        assert set(r["candidates"]) == {(1, 0), (2, 0), (3, 0), (4, 0), (0, 32), (0, 16)}
         assert sim.get_option(r["option"]) == r["best"][0]
         if r["best"][1]:
             assert sim.get_option(r["option2"]) == r["best"][1]
@@ -142,8 +142,9 @@ def test_autotune_picks_a_candidate_and_keeps_results(form):
     after = sim.simulate(xs, [2.0, 4.0], [3, 4])
     sim.check()
     # fused and split gather kernels differ by the FP16 rounding of G in the split
-    # one; each side stays within the 16-bit bound of the FP64 oracle
-    tol = SPLIT_VS_FUSED if form == "gather" else 1e-6
+    # ones and the FP16 sums of kernel 4; each side stays within the 16-bit bound of
+    # the FP64 oracle
+    tol = TOL_BF16 if form == "gather" else 1e-6
     for u, v in zip(before, after):
         close(v.cpu().numpy(), u.cpu().numpy(), tol)
 
@@ -167,7 +168,7 @@ def test_blur_then_warp_order(prec, form):
         close(ys[i].cpu().numpy(), ref.y, tol, i)
 
 
-@pytest.mark.parametrize("split_kernel", [1, 2, 3])
+@pytest.mark.parametrize("split_kernel", [1, 2, 3, 4])
 @pytest.mark.parametrize("c", [3, 1])
 def test_split_gather_matches_oracle_and_fused(c, split_kernel):
     """Network kernel, then a blur-only tensor-core gather (1: four accumulating warps per
@@ -189,8 +190,10 @@ def test_split_gather_matches_oracle_and_fused(c, split_kernel):
     yb = split.simulate(xd, dr, seeds)
     fused.check()
     split.check()
+    # kernel 4's FP16 sums (3e-4 to 1e-3 relative) on top of the FP16 rounding of G
+    tol = TOL_BF16 if split_kernel == 4 else SPLIT_VS_FUSED
     for i in range(len(xs)):
-        close(yb[i].cpu().numpy(), ya[i].cpu().numpy(), SPLIT_VS_FUSED, i)
+        close(yb[i].cpu().numpy(), ya[i].cpu().numpy(), tol, i)
     for i in (0, 1):
         ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
                                     CorrParams(8, (16.0,)), (33, 33), form="gather")
@@ -200,7 +203,7 @@ def test_split_gather_matches_oracle_and_fused(c, split_kernel):
     assert torch.equal(alone, yb[1])
 
 
-@pytest.mark.parametrize("split_kernel", [1, 2, 3])
+@pytest.mark.parametrize("split_kernel", [1, 2, 3, 4])
 def test_split_gather_blur_then_warp_and_graphs(split_kernel):
     shapes = [(96, 160), (70, 130)]
     xs = [torch.from_numpy(x).cuda() for x in _frames(shapes, first=2500)]

@@ -49,12 +49,13 @@ def test_tc_network_stage(prec, h, w):
     close(beta, ref, TOL_BF16)
 
 
-@pytest.mark.parametrize("split", [1, 2, 3, 0])
+@pytest.mark.parametrize("split", [1, 2, 3, 4, 0])
 @pytest.mark.parametrize("c", [3, 1])
 @pytest.mark.parametrize("h,w", [(40, 130), (33, 64), (1, 1), (70, 300)])
 def test_tc_blur_stage_fp16(c, h, w, split):
-    """Every gather kernel: the two blur-only ones fed 16-bit beta (split = 1, the
-    default, and split = 2, the fragment kernel) and the fused one (split = 0)."""
+    """Every gather kernel: the four blur-only ones fed 16-bit beta (split = 1, the
+    default; 2 and 3, the fragment kernels; 4, packed FP16 products) and the fused one
+    (split = 0)."""
     sim = _sim("fp16")
     sim.set_option("gather_split", split)
     rng = np.random.default_rng(31)
@@ -132,6 +133,49 @@ def test_tc_full_size_frame_fp16():
     sim = _sim("fp16")
     x = inputs.blob_image(512, 512, 3, 1000)
     (y,) = sim.simulate([torch.from_numpy(x).cuda()], [3.0], [10**6])
+    ref = oracle.frame.simulate(x.astype(np.float64), 10**6, 3.0, cfg2()["H"], cfg2()["layers"],
+                                CorrParams(8, (16.0,)), (33, 33), form="gather")
+    close(y.cpu().numpy(), ref.y, TOL_BF16)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("c,h,w", [(3, 48, 160), (1, 37, 150)])
+def test_tc_blur_stage_h2_rounding_points(prec, c, h, w):
+    """The packed-FP16 gather kernel (4) against an emulation of its arithmetic in its order
+    (tests/kernel_emulation.py): beta and H rounded to the operand type, G and x_w to FP16,
+    FP16 sums of 12 products (two per chunk, channel and row, by tap-column parity) flushed
+    into FP32, tap column 32 as FP32 sums, the groups' sums added in order.  The tensor core's
+    FP32 sums for G differ from the emulation's FP64 G in the last bit, which now and then
+    flips G's FP16 rounding and, through the FP16 sums, an FP16 ulp of a partial sum (2.5e-5
+    measured with sums of 24 products).  FP32 sums of the same products (kernel 1's
+    arithmetic) are 2.3e-4 from the emulation on these inputs, four times the tolerance, so
+    the test tells the two apart.  The odd last row pair and the ragged column tail are
+    covered."""
+    import kernel_emulation
+
+    sim = _sim(prec)
+    sim.set_option("gather_split", 4)
+    rng = np.random.default_rng(33)
+    xw = inputs.blob_image(h, w, c, 1005)
+    beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
+    y = sim.stage_blur(torch.from_numpy(xw).cuda(), torch.from_numpy(beta).cuda())
+    sim.check()
+    y = y.cpu().numpy()
+    rnd = bf16 if prec == "bf16" else (lambda v: v.astype(np.float16).astype(np.float64))
+    emu = kernel_emulation.gather_h2(xw, beta, cfg2()["H"], rnd)
+    close(y, emu, 6e-5)
+    ref = oracle.blur.gather(xw.astype(np.float64), beta.astype(np.float64), cfg2()["H"], 33, 33)
+    assert rel(emu, ref) > 1e-4  # the FP16 sums are what the emulation models
+
+
+@pytest.mark.parametrize("split", [4])
+def test_tc_full_size_frame_fp16_kernel4(split):
+    """One 512 x 512 RGB frame through the packed-FP16 gather kernel, whole frame checked."""
+    sim = _sim("fp16")
+    sim.set_option("gather_split", split)
+    x = inputs.blob_image(512, 512, 3, 1000)
+    (y,) = sim.simulate([torch.from_numpy(x).cuda()], [3.0], [10**6])
+    sim.check()
     ref = oracle.frame.simulate(x.astype(np.float64), 10**6, 3.0, cfg2()["H"], cfg2()["layers"],
                                 CorrParams(8, (16.0,)), (33, 33), form="gather")
     close(y.cpu().numpy(), ref.y, TOL_BF16)

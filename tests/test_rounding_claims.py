@@ -35,3 +35,31 @@ def test_g_rounding_bound():
     normal = np.abs(g) >= 2.0**-14
     assert np.all(np.abs(g16 - g)[normal] <= 2.0**-11 * np.abs(g)[normal])
     assert np.all(np.abs(g16 - g)[~normal] <= 2.0**-25)
+
+
+def test_packed_f16_sums_error_budget():
+    """The packed-FP16 gather kernel (gather_split = 4) keeps FP16 sums of 12 tap products:
+    on the blur-stage inputs of the GPU tests its emulated arithmetic stays within 1e-3
+    relative L2 of the exact gather (the 16-bit tolerance is 2e-3), and the FP16 sums move the
+    result by 1e-4 .. 1e-3 against FP32 sums of the same FP16 products (kernel 1's arithmetic,
+    itself within 4e-4 of the exact gather)."""
+    import oracle
+    from paper_2107_11627_gb300 import inputs
+
+    import kernel_emulation
+
+    z, dr0 = inputs.dictionary_draws(600, 35, (0.5, 6.0), 2021)
+    H, _ = oracle.psf.make_basis(z, dr0, K=100, taps=33)
+    rng = np.random.default_rng(31)
+    h, w = 33, 64
+    x = inputs.blob_image(h, w, 3, 1003)
+    beta = (rng.normal(0.0, 0.05, size=(h, w, 100)) + 0.3 * (np.arange(100) == 0)).astype(np.float32)
+    f16 = lambda v: v.astype(np.float16).astype(np.float64)
+    ref = oracle.blur.gather(x.astype(np.float64), beta.astype(np.float64), H, 33, 33)
+    emu = kernel_emulation.gather_h2(x, beta, H, f16)
+    g16 = f16(f16(beta.reshape(h * w, -1).astype(np.float64)) @ f16(H)).reshape(h, w, -1)
+    fp32_sums = oracle.blur.gather(f16(x.astype(np.float64)), g16.reshape(h * w, -1), np.eye(33 * 33), 33, 33)
+    rel = lambda a, b=ref: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(emu) < 1e-3, rel(emu)
+    assert rel(fp32_sums) < 4e-4, rel(fp32_sums)
+    assert 1e-4 < rel(emu, fp32_sums) < 1e-3, rel(emu, fp32_sums)
