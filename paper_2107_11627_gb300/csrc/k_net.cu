@@ -101,6 +101,13 @@ __device__ __forceinline__ int anchor_off(int e2) {
 }
 
 constexpr int kPre = 5;  // anchor-row elements per thread loaded one unit ahead (covers 18 anchors)
+constexpr int kRowStride = 36;  // floats per interpolated anchor in shared memory (33 modes, 16-byte rows)
+
+// shared-memory index of element e2 (anchor e2 / 33, mode e2 % 33) of an interpolated anchor row
+__device__ __forceinline__ int arow_idx(int e2) {
+    const int ax = e2 / kHiModes;
+    return ax * kRowStride + (e2 - ax * kHiModes);
+}
 
 template <int FMT>  // operand type: 0 FP16, 1 BF16
 __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant__ Params p) {
@@ -220,25 +227,35 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
 #pragma unroll
                 for (int q = 0; q < kPre; ++q) {
                     const int e2 = tid + 128 * q;
-                    if (e2 < nax * kHiModes) arow[e2] = (1.0f - fy) * pa[q] + fy * pb[q];
+                    if (e2 < nax * kHiModes) arow[arow_idx(e2)] = (1.0f - fy) * pa[q] + fy * pb[q];
                 }
                 for (int e2 = tid + 128 * kPre; e2 < nax * kHiModes; e2 += 128) {
                     const int off = anchor_off(e2);
-                    arow[e2] = (1.0f - fy) * __ldg(g.a + off) + fy * __ldg(g.b + off);
+                    arow[arow_idx(e2)] = (1.0f - fy) * __ldg(g.a + off) + fy * __ldg(g.b + off);
                 }
                 ptx::named_bar(1 + slot, 128);
                 const int gj = min(col, p.W - 1);
                 const int ax = gj / p.s - ax0;
                 const float fx = (float)(gj - (ax + ax0) * p.s) * p.inv_s;
-                const float *r0p = arow + ax * kHiModes;
-                const float *r1p = r0p + (ax + 1 < nax ? kHiModes : 0);
+                const float4 *r0p = (const float4 *)(arow + ax * kRowStride);
+                const float4 *r1p = r0p + (ax + 1 < nax ? kRowStride / 4 : 0);
 #pragma unroll
                 for (int g = 0; g < kK1 / 8; ++g) {
                     float v[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int k = 8 * g + j;
-                        v[j] = k < kHiModes ? (1.0f - fx) * r0p[k] + fx * r1p[k] : 0.f;
+                    for (int h = 0; h < 2; ++h) {
+                        const int k4 = 2 * g + h;  // modes 4 k4 .. 4 k4 + 3
+                        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+                        if (4 * k4 < kHiModes) {
+                            a0 = r0p[k4];
+                            a1 = r1p[k4];
+                        }
+                        const float e[4][2] = {{a0.x, a1.x}, {a0.y, a1.y}, {a0.z, a1.z}, {a0.w, a1.w}};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int k = 4 * k4 + j;  // column 33 = 1: the weight image carries b1 there
+                            v[4 * h + j] = k < kHiModes ? (1.0f - fx) * e[j][0] + fx * e[j][1] : (k == kHiModes ? 1.f : 0.f);
+                        }
                     }
                     uint4 q;
                     q.x = pack2(v[0], v[1], FMT);
@@ -279,16 +296,23 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {  // k-group c32 / 8 + g
                         uint32_t w4[4];
+                        if (L == 0) {  // b1 came through the tensor core (operand column 33)
 #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            const float4 bb = bv[2 * g + j];
-                            float h0, h1, h2, h3;
-                            tcc::add2(__uint_as_float(d[8 * g + 4 * j]), __uint_as_float(d[8 * g + 4 * j + 1]), bb.x,
-                                      bb.y, h0, h1);
-                            tcc::add2(__uint_as_float(d[8 * g + 4 * j + 2]), __uint_as_float(d[8 * g + 4 * j + 3]),
-                                      bb.z, bb.w, h2, h3);
-                            w4[2 * j] = tcc::pack2_relu(h0, h1, FMT);  // ReLU in the conversion
-                            w4[2 * j + 1] = tcc::pack2_relu(h2, h3, FMT);
+                            for (int j = 0; j < 4; ++j)
+                                w4[j] = tcc::pack2_relu(__uint_as_float(d[8 * g + 2 * j]), __uint_as_float(d[8 * g + 2 * j + 1]),
+                                                        FMT);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                const float4 bb = bv[2 * g + j];
+                                float h0, h1, h2, h3;
+                                tcc::add2(__uint_as_float(d[8 * g + 4 * j]), __uint_as_float(d[8 * g + 4 * j + 1]), bb.x,
+                                          bb.y, h0, h1);
+                                tcc::add2(__uint_as_float(d[8 * g + 4 * j + 2]), __uint_as_float(d[8 * g + 4 * j + 3]),
+                                          bb.z, bb.w, h2, h3);
+                                w4[2 * j] = tcc::pack2_relu(h0, h1, FMT);  // ReLU in the conversion
+                                w4[2 * j + 1] = tcc::pack2_relu(h2, h3, FMT);
+                            }
                         }
                         *(uint4 *)(abuf + (c32 / 8 + g) * (kTile * 16) + m * 16) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
                     }
@@ -480,7 +504,7 @@ static int net_layout(const p2s_ctx *ctx, int s, int W, Params *p) {
     const Item16 *it = (const Item16 *)ctx->tc_items.data();
     for (int i = 0; i < ctx->tc.n_mlp; ++i) w += it[i].bytes;
     const int max_ax = std::min((kTile - 1) / s + 3, (W - 1) / s + 2);
-    const uint32_t row_bytes = ((uint32_t)max_ax * kHiModes * 4 + 127) & ~127u;
+    const uint32_t row_bytes = ((uint32_t)max_ax * kRowStride * 4 + 127) & ~127u;
     const uint32_t fixed_tail = (uint32_t)(ctx->tc.h1p + ctx->tc.h2p) * 4 + kNBar * 8 + 16 + 1024;
     const uint32_t offA = (w + 1023) & ~1023u;
     int ns = kMaxSlots;

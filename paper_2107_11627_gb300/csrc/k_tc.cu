@@ -793,7 +793,14 @@ p2s_status tc_prepare(p2s_ctx *ctx) {
     const int outp[3] = {h1p, h2p, n3};
     for (int l = 0; l < 3; ++l) {
         const std::vector<double> &W = ctx->W[l];
-        auto w_at = [&](int n, int k) -> double { return (n < outs[l] && k < ins[l]) ? W[(size_t)n * ins[l] + k] : 0.0; };
+        // layer 1 also carries b1 in input column 33 (one of the padding columns up to 48): the
+        // network kernel sets that operand column to 1 and the tensor core adds the bias; the
+        // fused kernel leaves it 0 and adds b1 itself
+        auto w_at = [&](int n, int k) -> double {
+            if (n >= outs[l]) return 0.0;
+            if (k < ins[l]) return W[(size_t)n * ins[l] + k];
+            return (l == 0 && k == kHiModes) ? ctx->b[0][n] : 0.0;
+        };
         add_image(outp[l], inp[l], [&](int n, int k) { return to_half_bits(w_at(n, k), fmt); });
         if (split)
             add_image(outp[l], inp[l], [&](int n, int k) {
