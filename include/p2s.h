@@ -150,11 +150,18 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
 /* As p2s_simulate, but frames[i].data and out[i].data are HOST pointers: the
  * call stages them through device buffers (host->device copy, path,
  * device->host copy) and returns when out[] is written.  From 32 frames on,
- * the frames go in chunks of at least 16 (at most 4 chunks): a chunk's
+ * the frames go in chunks: an eighth of them first and last, the rest in at
+ * most 3 chunks of at least 16 (64 frames: 8 + 16 + 16 + 16 + 8).  A chunk's
  * host->device copy overlaps the path of the chunk before it and its
  * device->host copy the path of the chunk after, on two copy streams owned by
- * the context; the path runs on `stream`.  Results equal p2s_simulate's.
- * Pinned host memory gives full copy bandwidth and overlap. */
+ * the context.  The chunks' paths alternate between `stream` and a second
+ * compute stream owned by the context (one stream in graph mode), so that a
+ * chunk's kernels fill the SMs the previous chunk's last wave leaves idle.
+ * Results equal p2s_simulate's.  Pinned host memory gives full copy bandwidth
+ * and overlap. */
+p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
+                             const unsigned long long *seeds, const p2s_image *out, void *stream);
+
 /* Wavelength-dependent colour (Sec. 3.5): RGB frames whose channels are blurred
  * with three PSF sets, one per wavelength (the paper's 570, 540 and 450 nm for
  * R, G, B), at three times the cost of one.  ctx3[c] is channel c's context:
@@ -170,9 +177,6 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
  * p2s_simulate, plus EINVAL for mismatched contexts or C != 3. */
 p2s_status p2s_simulate_spectral(p2s_ctx *const *ctx3, const p2s_image *frames, int n, const float *D_over_r0,
                                  const unsigned long long *seeds, const p2s_image *out, void *stream);
-
-p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
-                             const unsigned long long *seeds, const p2s_image *out, void *stream);
 
 /* ---- stage entry points: each step alone, for per-stage parity ---------- */
 

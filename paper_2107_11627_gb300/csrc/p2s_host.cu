@@ -368,6 +368,7 @@ void p2s_destroy(p2s_ctx *ctx) {
         if (kv.second) cudaGraphExecDestroy(kv.second);
     cudaFree(ctx->arena);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
     for (cudaStream_t cs : ctx->copy_stream)
         if (cs) cudaStreamDestroy(cs);
     for (cudaEvent_t e : ctx->host_ev) cudaEventDestroy(e);
@@ -1174,12 +1175,27 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
     cudaStream_t s = (cudaStream_t)stream;
     // The frames go in chunks: chunk k's host->device copy (copy stream 0) overlaps the
     // path of chunk k - 1 (the caller's stream), whose device->host copy (copy stream 1)
-    // overlaps the path of chunk k + 1.  Chunks of at least 16 frames keep the persistent
-    // launches full; at most 4 chunks.
-    const int nch = n >= 32 ? std::min(4, n / 16) : 1;
+    // overlaps the path of chunk k + 1.  Only the first chunk's copy in and the last
+    // chunk's copy out are exposed, so those two chunks take an eighth of the frames each
+    // and the rest go in chunks of at least 16 frames (full persistent launches), at most
+    // 3 of them: 64 frames as 8 + 16 + 16 + 16 + 8.
+    std::vector<int> bounds{0};
+    if (n >= 32) {
+        const int edge = n / 8, mid = n - 2 * edge, nmid = std::max(1, std::min(3, mid / 16));
+        bounds.push_back(edge);
+        for (int k = 1; k <= nmid; ++k) bounds.push_back(edge + (int)((long long)mid * k / nmid));
+    }
+    bounds.push_back(n);
+    bounds.erase(std::unique(bounds.begin(), bounds.end()), bounds.end());
+    const int nch = (int)bounds.size() - 1;
     for (int i = 0; i < 2; ++i)
         if (!ctx->copy_stream[i]) P2S_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream[i], cudaStreamNonBlocking));
-    while ((int)ctx->host_ev.size() < 2 * nch + 2) {
+    // Chunks alternate between the caller's stream and a second compute stream, so that the
+    // next chunk's kernels take the SMs the current chunk's last wave leaves idle.  Graph
+    // mode keeps one stream: its captured launches share the context's scratch arena.
+    const bool two = nch > 1 && !ctx->use_graphs;
+    if (two && !ctx->aux_stream) P2S_CUDA(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+    while ((int)ctx->host_ev.size() < 2 * nch + 3) {
         cudaEvent_t e;
         P2S_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ctx->host_ev.push_back(e);
@@ -1192,6 +1208,7 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
     P2S_CUDA(cudaMallocAsync((void **)&buf, total + 256, s));
     P2S_CUDA(cudaEventRecord(ev_alloc, s));
     P2S_CUDA(cudaStreamWaitEvent(cin, ev_alloc, 0));
+    if (two) P2S_CUDA(cudaStreamWaitEvent(ctx->aux_stream, ev_alloc, 0));
     std::vector<p2s_image> din(n), dout(n);
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
@@ -1203,7 +1220,7 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
         dout[i].data = (float *)(buf + off);
         off += (bytes + 255) & ~(size_t)255;
     }
-    auto chunk_begin = [&](int k) { return (int)((long long)n * k / nch); };
+    auto chunk_begin = [&](int k) { return bounds[k]; };
     // all host->device copies, chunk by chunk, each chunk's end marked
     for (int k = 0; k < nch && st == P2S_OK; ++k) {
         for (int i = chunk_begin(k); i < chunk_begin(k + 1); ++i) {
@@ -1219,10 +1236,11 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
     // the path per chunk on the caller's stream, each chunk's results copied back
     for (int k = 0; k < nch && st == P2S_OK; ++k) {
         const int i0 = chunk_begin(k), i1 = chunk_begin(k + 1);
-        P2S_CUDA(cudaStreamWaitEvent(s, ctx->host_ev[2 + 2 * k], 0));
-        st = p2s_simulate(ctx, din.data() + i0, i1 - i0, d_over_r0 + i0, seeds + i0, dout.data() + i0, stream);
+        cudaStream_t cs = (two && (k & 1)) ? ctx->aux_stream : s;
+        P2S_CUDA(cudaStreamWaitEvent(cs, ctx->host_ev[2 + 2 * k], 0));
+        st = p2s_simulate(ctx, din.data() + i0, i1 - i0, d_over_r0 + i0, seeds + i0, dout.data() + i0, (void *)cs);
         if (st != P2S_OK) break;
-        P2S_CUDA(cudaEventRecord(ctx->host_ev[3 + 2 * k], s));
+        P2S_CUDA(cudaEventRecord(ctx->host_ev[3 + 2 * k], cs));
         P2S_CUDA(cudaStreamWaitEvent(cout, ctx->host_ev[3 + 2 * k], 0));
         for (int i = i0; i < i1; ++i) {
             const size_t bytes = (size_t)out[i].H * out[i].W * out[i].C * 4;
@@ -1233,7 +1251,11 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
             }
         }
     }
-    // the buffers are released on the caller's stream once every copy is done
+    // the buffers are released on the caller's stream once every copy and chunk is done
+    if (two) {
+        cudaEventRecord(ctx->host_ev[2 + 2 * nch], ctx->aux_stream);
+        cudaStreamWaitEvent(s, ctx->host_ev[2 + 2 * nch], 0);
+    }
     cudaEventRecord(ev_done, cout);
     cudaStreamWaitEvent(s, ev_done, 0);
     cudaEventRecord(ev_done, cin);

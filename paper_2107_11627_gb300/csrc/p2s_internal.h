@@ -141,6 +141,7 @@ struct p2s_ctx {
     cudaEvent_t cap_ev[2] = {nullptr, nullptr};
     // p2s_simulate_host: copy streams (host->device, device->host) and per-chunk events
     cudaStream_t copy_stream[2] = {nullptr, nullptr};
+    cudaStream_t aux_stream = nullptr;  // second compute stream of p2s_simulate_host
     std::vector<cudaEvent_t> host_ev;
     std::map<std::string, cudaGraphExec_t> graphs;
     long long graph_updates = 0, graph_instantiations = 0;
