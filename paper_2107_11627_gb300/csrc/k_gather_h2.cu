@@ -65,7 +65,7 @@ __host__ __device__ constexpr uint32_t colBeta(int r) { return r ? 56u : 0u; }
 __host__ __device__ constexpr uint32_t colDB(int h) { return h ? 320u : 128u; }
 
 constexpr int kOffRing = 0;
-constexpr int kOffX = kOffRing + kSlots * kSlot;           // uint2 [kXRing][kTC]: FP16 (R, G), (B, 0)
+constexpr int kOffX = kOffRing + kSlots * kSlot;           // [kXRing][kTC] pixels (8 B for RGB, 4 B for one channel)
 constexpr int kOffBeta = kOffX + kXRing * kTC * 8;         // [2 rows][14][128][16 B]
 constexpr int kOffXchg = kOffBeta + 2 * kBetaRow;          // float [3][128][6]
 enum Bar { kFull0 = 0, kEmpty0 = 3, kBStaged = 6, kBFree = 7, kBetaIn0 = 8, kPairDone0 = 10, kDFull0 = 12, kDEmpty0 = 14,
@@ -109,11 +109,31 @@ __device__ __forceinline__ int frame_of(const Params &p, int tile) {
     return lo;
 }
 
-// x pixel as FP16: (R, G) and (B, 0)
-__device__ __forceinline__ uint2 encode_px(float r, float g, float b) {
-    const __half2 rg = __floats2half2_rn(r, g), b0 = __floats2half2_rn(b, 0.f);
-    return make_uint2(*reinterpret_cast<const uint32_t *>(&rg), *reinterpret_cast<const uint32_t *>(&b0));
+// x_w in shared memory, one entry per tile pixel: three channels as 8 bytes of FP16,
+// (R, G) and (B, 0); one channel as one 32-bit word (R, 0), half the shared-memory
+// traffic of the 8-byte form (a warp's 8-byte loads take two wavefronts, its 4-byte
+// loads one).
+template <int C>
+struct XPix {
+    using T = uint2;
+};
+template <>
+struct XPix<1> {
+    using T = uint32_t;
+};
+__device__ __forceinline__ uint32_t half_pair(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
+template <int C>
+__device__ __forceinline__ typename XPix<C>::T encode_px(float r, float g, float b) {
+    if constexpr (C == 3)
+        return make_uint2(half_pair(r, g), half_pair(b, 0.f));
+    else
+        return half_pair(r, 0.f);
+}
+__device__ __forceinline__ uint32_t rg_of(uint2 v) { return v.x; }
+__device__ __forceinline__ uint32_t rg_of(uint32_t v) { return v; }
 
 // The packed tap products of 8 tap pairs: G of row r in g0, of row r + 1 in g1, x_w in v;
 // a[u & 1][ch] = (channel ch of row r, of row r + 1), x_w broadcast to both halves (the
@@ -121,13 +141,13 @@ __device__ __forceinline__ uint2 encode_px(float r, float g, float b) {
 // channel, by the parity of the tap column, halve the dependent chains.  One conversion
 // per pair.
 template <int C>
-__device__ __forceinline__ void tap_pairs8(const uint32_t (&g0)[8], const uint32_t (&g1)[8], const uint2 (&v)[8],
-                                           uint32_t (&a)[2][3]) {
+__device__ __forceinline__ void tap_pairs8(const uint32_t (&g0)[8], const uint32_t (&g1)[8],
+                                           const typename XPix<C>::T (&v)[8], uint32_t (&a)[2][3]) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         const uint32_t g2 = tcc::pack_f16x2(__uint_as_float(g0[u]), __uint_as_float(g1[u]));
-        tcc::hfma2_bcast<false>(a[u & 1][0], g2, v[u].x);
-        if (C == 3) {
+        tcc::hfma2_bcast<false>(a[u & 1][0], g2, rg_of(v[u]));
+        if constexpr (C == 3) {
             tcc::hfma2_bcast<true>(a[u & 1][1], g2, v[u].x);
             tcc::hfma2_bcast<false>(a[u & 1][2], g2, v[u].y);
         }
@@ -144,7 +164,8 @@ __device__ __forceinline__ int xring_row(int s0, int d) {
 // tile row 2 rp + 32 - ty, tile column col + 32 - tx; tile row tr sits in ring row
 // tr mod kXRing.
 template <int C>
-__device__ __forceinline__ void accumulate_pair(const uint2 *xs, uint32_t lane_base, int col, int rp, int grp,
+__device__ __forceinline__ void accumulate_pair(const typename XPix<C>::T *xs, uint32_t lane_base, int col, int rp,
+                                                int grp,
                                                 uint32_t bar0, uint32_t &uses, bool &ok, const Ctl &ctl, int lane,
                                                 float (&acc)[2][3]) {
     auto BAR = [&](int i) { return bar0 + 8u * (uint32_t)i; };
@@ -167,7 +188,7 @@ __device__ __forceinline__ void accumulate_pair(const uint2 *xs, uint32_t lane_b
                 ptx::tmem_ld8(buf + 96 + 32 * j + T0, g1);
                 // tap pair p = 3 c + j: row r at ty = p - 1, row r + 1 at ty = p
                 const int base = xring_row(s0, 33 - (3 * c + j)) * kTC + col + 32 - T0;
-                uint2 v[8];
+                typename XPix<C>::T v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = xs[base - u];
                 ptx::tmem_wait_ld_dep(g0);
@@ -183,7 +204,7 @@ __device__ __forceinline__ void accumulate_pair(const uint2 *xs, uint32_t lane_b
             ptx::tmem_ld9(buf + 32 + 9 * grp, h0);
             ptx::tmem_ld9(buf + 96 + 9 * grp, h1);
             const int base = s0 * kTC + col + 32 - T0;
-            uint2 v[8];
+            typename XPix<C>::T v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 v[u] = xs[base - u];
@@ -199,15 +220,16 @@ __device__ __forceinline__ void accumulate_pair(const uint2 *xs, uint32_t lane_b
                 if (q < nq) {
                     const int ty = 9 * grp + q;
                     const uint32_t gp = tcc::pack_f16x2(__uint_as_float(h0[q]), __uint_as_float(h1[q]));
-                    const uint2 x0 = xs[xring_row(s0, 32 - ty) * kTC + col], x1 = xs[xring_row(s0, 33 - ty) * kTC + col];
-                    if (C == 3) {
+                    const typename XPix<C>::T x0 = xs[xring_row(s0, 32 - ty) * kTC + col],
+                                              x1 = xs[xring_row(s0, 33 - ty) * kTC + col];
+                    if constexpr (C == 3) {
                         tcc::fma_mix_x2<false>(x0.x, gp, acc[0][0], acc[0][1]);
                         tcc::fma_mix_x1<false>(x0.y, gp, acc[0][2]);
                         tcc::fma_mix_x2<true>(x1.x, gp, acc[1][0], acc[1][1]);
                         tcc::fma_mix_x1<true>(x1.y, gp, acc[1][2]);
                     } else {
-                        tcc::fma_mix_x1<false>(x0.x, gp, acc[0][0]);
-                        tcc::fma_mix_x1<true>(x1.x, gp, acc[1][0]);
+                        tcc::fma_mix_x1<false>(x0, gp, acc[0][0]);
+                        tcc::fma_mix_x1<true>(x1, gp, acc[1][0]);
                     }
                 }
             }
@@ -230,7 +252,8 @@ __global__ void __launch_bounds__(kThreads, 1) gather_h2_kernel(const __grid_con
     // aligned by pointer arithmetic on the __shared__ array (accesses stay ld/st.shared)
     uint8_t *sm = smem_raw + ((1024u - (uint32_t)((uintptr_t)smem_raw & 1023u)) & 1023u);
     const uint32_t sbase = ptx::smem_u32(sm);
-    uint2 *xs = (uint2 *)(sm + kOffX);
+    using XT = typename XPix<C>::T;
+    XT *xs = (XT *)(sm + kOffX);
     float *xchg = (float *)(sm + kOffXchg);
     const uint32_t bar0 = sbase + kOffBar;
     uint32_t *tmem_holder = (uint32_t *)(sm + kOffMisc);
@@ -398,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1) gather_h2_kernel(const __grid_con
                 const int tr = i / kTC, tcol = i - tr * kTC;
                 float r, g, b;
                 load_px(tr, tcol, r, g, b);
-                xs[i] = encode_px(r, g, b);
+                xs[i] = encode_px<C>(r, g, b);
             }
             ptx::named_bar(1, kEpi);
             for (int rp = 0; rp < npair; ++rp) {
@@ -416,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) gather_h2_kernel(const __grid_con
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) acc[i][ch] = 0.f;
                 accumulate_pair<C>(xs, lane_base, col, rp, grp, bar0, uses, ok, ctl, lane, acc);
-                if (stage) xs[(ntr % kXRing) * kTC + ncol] = encode_px(nr, ng, nb);
+                if (stage) xs[(ntr % kXRing) * kTC + ncol] = encode_px<C>(nr, ng, nb);
                 // ---- add the four groups' partial sums, write the row pair ----
                 if (grp > 0) {
                     float *xc = xchg + (grp - 1) * kStrip * 6;
