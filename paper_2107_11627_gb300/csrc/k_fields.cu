@@ -203,11 +203,10 @@ __device__ __forceinline__ float2 tw_at(const float2 *tw, int m, int N, bool inv
     return w;
 }
 
-// v[i] <- sum_k v[k] w_P^(i k) (w_P = exp(-+2 pi i / P)), P a power of two, by an iterative
-// radix-2 decimation in time on the bit-reversed order; N is the table's length.
+// v[i] <- sum_k v[k] w_P^(i k) (w_P = exp(-+2 pi i / P)), P >= 2 a power of two, by an
+// iterative radix-2 decimation in time on the bit-reversed order; N is the table's length.
 template <int P>
-__device__ __forceinline__ void dft_in_thread(float2 (&v)[P], const float2 *tw, int N, bool inverse) {
-    if constexpr (P == 1) return;
+__device__ __forceinline__ void dft_in_thread_pow2(float2 (&v)[P], const float2 *tw, int N, bool inverse) {
     float2 a[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -229,6 +228,12 @@ __device__ __forceinline__ void dft_in_thread(float2 (&v)[P], const float2 *tw, 
             }
 #pragma unroll
     for (int i = 0; i < P; ++i) v[i] = a[i];
+}
+
+// the same for any power of two P (P = 1: nothing to do)
+template <int P>
+__device__ __forceinline__ void dft_in_thread(float2 (&v)[P], const float2 *tw, int N, bool inverse) {
+    if constexpr (P > 1) dft_in_thread_pow2<P>(v, tw, N, inverse);
 }
 
 __device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {

@@ -38,6 +38,7 @@
 #include <cstring>
 #include <vector>
 
+#include "half_bits.h"
 #include "p2s_internal.h"
 #include "tc_common.cuh"
 #include "tc_ptx.cuh"
@@ -420,27 +421,6 @@ __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_const
     }
 }
 
-__host__ inline uint16_t half_bits(double v, int fmt) {
-    uint16_t u;
-    if (fmt == 1) {
-        __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-        std::memcpy(&u, &h, 2);
-    } else {
-        __half h = __float2half_rn((float)v);
-        std::memcpy(&u, &h, 2);
-    }
-    return u;
-}
-__host__ inline double from_bits(uint16_t u, int fmt) {
-    if (fmt == 1) {
-        __nv_bfloat16 h;
-        std::memcpy(&h, &u, 2);
-        return (double)__bfloat162float(h);
-    }
-    __half h;
-    std::memcpy(&h, &u, 2);
-    return (double)__half2float(h);
-}
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -498,10 +478,10 @@ p2s_status scatter_prepare(p2s_ctx *ctx) {
         for (int k = 0; k < kGroups * 8; ++k) {
             uint16_t v = 0;
             if (k < K) {
-                v = half_bits(ctx->H[(size_t)k * T + t], fmt);
+                v = to_half_bits(ctx->H[(size_t)k * T + t], fmt);
             } else if (k == K || k == K + 1) {
-                const uint16_t hi = half_bits(hb[t], fmt);
-                v = k == K ? hi : half_bits(hb[t] - from_bits(hi, fmt), fmt);
+                const uint16_t hi = to_half_bits(hb[t], fmt);
+                v = k == K ? hi : to_half_bits(hb[t] - from_half_bits(hi, fmt), fmt);
             }
             img[((size_t)(k / 8) * kHAll + r) * 8 + (k % 8)] = v;
         }

@@ -29,6 +29,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "half_bits.h"
 #include "p2s_internal.h"
 #include "tc_common.cuh"
 #include "tc_ptx.cuh"
@@ -563,28 +564,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_kernel(const __grid_constan
     }
 }
 
-__host__ inline uint16_t to_half_bits(double v, int fmt) {
-    if (fmt == 1) {
-        __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-        uint16_t u;
-        std::memcpy(&u, &h, 2);
-        return u;
-    }
-    __half h = __float2half_rn((float)v);
-    uint16_t u;
-    std::memcpy(&u, &h, 2);
-    return u;
-}
-__host__ inline double from_half_bits(uint16_t u, int fmt) {
-    if (fmt == 1) {
-        __nv_bfloat16 h;
-        std::memcpy(&h, &u, 2);
-        return (double)__bfloat162float(h);
-    }
-    __half h;
-    std::memcpy(&h, &u, 2);
-    return (double)__half2float(h);
-}
 
 // canonical K-major, no swizzle: (n, k) -> byte offset; rows N (multiple of 8)
 __host__ inline size_t canon(int n, int k, int N) { return (size_t)(k / 8) * (N * 16) + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2; }
