@@ -1086,18 +1086,31 @@ p2s_status p2s_simulate_spectral(p2s_ctx *const *ctx3, const p2s_image *frames, 
         pin[i] = p2s_image{(float *)(buf + off[i]), frames[i].H, frames[i].W, 1};
         pout[i] = p2s_image{(float *)(buf + total + off[i]), frames[i].H, frames[i].W, 1};
     }
+    // channel copies in one launch per run of consecutive frames of one size
+    std::vector<const float *> rgb_in(n), plane_out(n);
+    std::vector<float *> plane_in(n), rgb_out(n);
+    for (int i = 0; i < n; ++i) {
+        rgb_in[i] = frames[i].data;
+        plane_in[i] = pin[i].data;
+        plane_out[i] = pout[i].data;
+        rgb_out[i] = out[i].data;
+    }
+    auto copy_runs = [&](const std::vector<const float *> &src, const std::vector<float *> &dst, int ss, int so, int ds,
+                         int dof) -> p2s_status {
+        for (int i0 = 0; i0 < n;) {
+            int i1 = i0 + 1;
+            while (i1 < n && frames[i1].H == frames[i0].H && frames[i1].W == frames[i0].W) ++i1;
+            const p2s_status r = launch_channel_copy(src.data() + i0, dst.data() + i0, i1 - i0,
+                                                     (long long)frames[i0].H * frames[i0].W, ss, so, ds, dof, s);
+            if (r != P2S_OK) return r;
+            i0 = i1;
+        }
+        return P2S_OK;
+    };
     for (int c = 0; c < 3 && st == P2S_OK; ++c) {
-        for (int i = 0; i < n && st == P2S_OK; ++i) {
-            const float *f_src[1] = {frames[i].data};
-            float *f_dst[1] = {pin[i].data};
-            st = launch_channel_copy(f_src, f_dst, 1, (long long)frames[i].H * frames[i].W, 3, c, 1, 0, s);
-        }
+        st = copy_runs(rgb_in, plane_in, 3, c, 1, 0);
         if (st == P2S_OK) st = p2s_simulate(ctx3[c], pin.data(), n, d_over_r0, seeds, pout.data(), stream);
-        for (int i = 0; i < n && st == P2S_OK; ++i) {
-            const float *f_src[1] = {pout[i].data};
-            float *f_dst[1] = {out[i].data};
-            st = launch_channel_copy(f_src, f_dst, 1, (long long)frames[i].H * frames[i].W, 1, 0, 3, c, s);
-        }
+        if (st == P2S_OK) st = copy_runs(plane_out, rgb_out, 1, 0, 3, c);
     }
     cudaFreeAsync(buf, s);
     return st;
