@@ -10,6 +10,7 @@
 // column pass that the anchors use are kept.
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -291,13 +292,15 @@ constexpr int kFieldWarps = 8;
 // columns [0, Aw) kept in shared memory), then column pass (columns (2 c, 2 c + 1) of that
 // block filtered along y, rows [0, Ah) to f[frame][mode][y][x]).  One CTA per (mode, frame);
 // the same arithmetic as row_filter_kernel and col_filter_kernel.
+// Frames of one launch may differ in their anchor grids (one torus for all): each has its
+// own Ah x Aw and output block, and `pitch` is odd and at least every frame's Aw.
 template <int PW, int PH>
-__global__ void __launch_bounds__(32 * kFieldWarps, 1) field_kernel(FrameBatch fb, int Ah, int Aw, int pitch,
+__global__ void __launch_bounds__(32 * kFieldWarps, 1) field_kernel(FrameBatch fb, FieldFrames geo, int pitch,
                                                                   const float2 *__restrict__ twx,
                                                                   const float *__restrict__ gainx,
                                                                   const float2 *__restrict__ twy,
                                                                   const float *__restrict__ gainy,
-                                                                  const int *__restrict__ kernel_of_mode, float *f) {
+                                                                  const int *__restrict__ kernel_of_mode) {
     constexpr int Fw = 32 * PW, Fh = 32 * PH;
     extern __shared__ float sfm[];
     float *tb = sfm;                                   // [Fh][pitch]: the row pass's columns < Aw
@@ -306,6 +309,7 @@ __global__ void __launch_bounds__(32 * kFieldWarps, 1) field_kernel(FrameBatch f
     float2 *tx = (float2 *)(gy + Fh), *ty = tx + Fw / 2;
     const int mode = blockIdx.x, frame = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Ah = geo.ah[frame], Aw = geo.aw[frame];
     const int kk = kernel_of_mode[mode];
     for (int i = threadIdx.x; i < Fw; i += blockDim.x) gx[i] = gainx[(size_t)kk * Fw + i];
     for (int i = threadIdx.x; i < Fh; i += blockDim.x) gy[i] = gainy[(size_t)kk * Fh + i];
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(32 * kFieldWarps, 1) field_kernel(FrameBatch f
         }
     }
     __syncthreads();
-    float *ff = f + ((size_t)frame * kModes + mode) * Ah * Aw;
+    float *ff = geo.f[frame] + (size_t)mode * Ah * Aw;
     for (int cp = warp; 2 * cp < Aw; cp += kFieldWarps) {
         const int x0 = 2 * cp;
         const bool two = x0 + 1 < Aw;
@@ -376,20 +380,20 @@ __global__ void __launch_bounds__(32 * kFieldWarps, 1) field_kernel(FrameBatch f
 }
 
 // alpha(a) = (D/r0)^(5/6) L f(a): slot 0 (piston) = 0, slot l+1 = mode l + 2.
-__global__ void colour_kernel(FrameBatch fb, int A, const float *__restrict__ L, const float *__restrict__ f,
-                              float *alpha) {
+__global__ void colour_kernel(FrameBatch fb, FieldFrames geo, const float *__restrict__ L) {
     __shared__ float sL[kModes * kModes];
     for (int i = threadIdx.x; i < kModes * kModes; i += blockDim.x) sL[i] = L[i];
     __syncthreads();
     const int frame = blockIdx.y;
+    const int A = geo.ah[frame] * geo.aw[frame];
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A) return;
-    const float *ff = f + (size_t)frame * kModes * A + a;
+    const float *ff = geo.f[frame] + a;
     float v[kModes];
 #pragma unroll
     for (int l = 0; l < kModes; ++l) v[l] = ff[(size_t)l * A];
     const float sc = fb.scale[frame];
-    float *out = alpha + ((size_t)frame * A + a) * kAlphaStride;
+    float *out = geo.alpha[frame] + (size_t)a * kAlphaStride;
     out[0] = 0.0f;
 #pragma unroll
     for (int j = 0; j < kModes; ++j) {
@@ -413,35 +417,93 @@ p2s_status launch_noise(unsigned long long seed, int mode, int Fh, int Fw, float
 // The one-kernel filter for tori of 32 .. 256 points per axis whose row-pass block fits
 // in shared memory; false: use the two-pass kernels.
 template <int PW, int PH>
-static p2s_status launch_field_pw_ph(const FieldGeom &g, const FrameBatch &fb, int pitch, size_t smem,
-                                     const FilterTable *tw, const FilterTable *th, const int *kom, float *f,
-                                     cudaStream_t st) {
+static p2s_status launch_field_pw_ph(const FrameBatch &fb, const FieldFrames &geo, int pitch, size_t smem,
+                                     const FilterTable *tw, const FilterTable *th, const int *kom, cudaStream_t st) {
     P2S_CUDA(cudaFuncSetAttribute(field_kernel<PW, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    field_kernel<PW, PH><<<dim3(kModes, fb.n), 32 * kFieldWarps, smem, st>>>(fb, g.Ah, g.Aw, pitch, tw->twiddle,
-                                                                             tw->gain, th->twiddle, th->gain, kom, f);
+    field_kernel<PW, PH><<<dim3(kModes, fb.n), 32 * kFieldWarps, smem, st>>>(fb, geo, pitch, tw->twiddle, tw->gain,
+                                                                             th->twiddle, th->gain, kom);
     P2S_CUDA(cudaGetLastError());
     return P2S_OK;
 }
 
 template <int PW>
-static p2s_status launch_field_pw(int PH, const FieldGeom &g, const FrameBatch &fb, int pitch, size_t smem,
-                                  const FilterTable *tw, const FilterTable *th, const int *kom, float *f,
-                                  cudaStream_t st) {
+static p2s_status launch_field_pw(int PH, const FrameBatch &fb, const FieldFrames &geo, int pitch, size_t smem,
+                                  const FilterTable *tw, const FilterTable *th, const int *kom, cudaStream_t st) {
     switch (PH) {
-        case 1: return launch_field_pw_ph<PW, 1>(g, fb, pitch, smem, tw, th, kom, f, st);
-        case 2: return launch_field_pw_ph<PW, 2>(g, fb, pitch, smem, tw, th, kom, f, st);
-        case 4: return launch_field_pw_ph<PW, 4>(g, fb, pitch, smem, tw, th, kom, f, st);
-        default: return launch_field_pw_ph<PW, 8>(g, fb, pitch, smem, tw, th, kom, f, st);
+        case 1: return launch_field_pw_ph<PW, 1>(fb, geo, pitch, smem, tw, th, kom, st);
+        case 2: return launch_field_pw_ph<PW, 2>(fb, geo, pitch, smem, tw, th, kom, st);
+        case 4: return launch_field_pw_ph<PW, 4>(fb, geo, pitch, smem, tw, th, kom, st);
+        default: return launch_field_pw_ph<PW, 8>(fb, geo, pitch, smem, tw, th, kom, st);
     }
 }
 
-static bool field_kernel_fits(const FieldGeom &g, int *pitch, size_t *smem) {
+// The one-kernel filter serves tori of 32 .. 256 points per axis whose row-pass block
+// (Fh rows of the widest anchor grid, Aw_max) fits in shared memory.
+static bool field_kernel_fits(int Fh, int Fw, int Ah_max, int Aw_max, int *pitch, size_t *smem) {
     auto ok_len = [](int F) { return F == 32 || F == 64 || F == 128 || F == 256; };
-    if (!ok_len(g.Fw) || !ok_len(g.Fh) || g.Aw > g.Fw || g.Ah > g.Fh) return false;
-    *pitch = g.Aw | 1;  // odd: the column pass reads 32 rows of one column without bank conflicts
-    *smem = ((size_t)g.Fh * *pitch + (size_t)kFieldWarps * 2 * g.Fw + g.Fw + g.Fh) * sizeof(float) +
-            (size_t)(g.Fw / 2 + g.Fh / 2) * sizeof(float2);
+    if (!ok_len(Fw) || !ok_len(Fh) || Aw_max > Fw || Ah_max > Fh) return false;
+    *pitch = Aw_max | 1;  // odd: the column pass reads 32 rows of one column without bank conflicts
+    *smem = ((size_t)Fh * *pitch + (size_t)kFieldWarps * 2 * Fw + Fw + Fh) * sizeof(float) +
+            (size_t)(Fw / 2 + Fh / 2) * sizeof(float2);
     return *smem <= 160 * 1024;
+}
+static bool field_kernel_fits(const FieldGeom &g, int *pitch, size_t *smem) {
+    return field_kernel_fits(g.Fh, g.Fw, g.Ah, g.Aw, pitch, smem);
+}
+
+// filter (one kernel) and colour over frames of one torus, each with its own anchor grid
+static p2s_status run_field_group(p2s_ctx *ctx, int Fh, int Fw, const FrameBatch &fb, const FieldFrames &geo,
+                                  int pitch, size_t fsmem, cudaStream_t st) {
+    const FilterTable *th = nullptr, *tw = nullptr;
+    p2s_status s = filter_table(ctx, Fh, &th);
+    if (s != P2S_OK) return s;
+    if ((s = filter_table(ctx, Fw, &tw)) != P2S_OK) return s;
+    double cells = 0.0;
+    int max_a = 0;
+    for (int k = 0; k < fb.n; ++k) {
+        cells += (double)geo.ah[k] * geo.aw[k];
+        max_a = std::max(max_a, geo.ah[k] * geo.aw[k]);
+    }
+    {
+        ProfScope pf(ctx, st, "fields_filter", 0.0, cells * kModes * 4);
+        const int PW = Fw / 32, PH = Fh / 32;
+        p2s_status rs;
+        switch (PW) {
+            case 1: rs = launch_field_pw<1>(PH, fb, geo, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, st); break;
+            case 2: rs = launch_field_pw<2>(PH, fb, geo, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, st); break;
+            case 4: rs = launch_field_pw<4>(PH, fb, geo, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, st); break;
+            default: rs = launch_field_pw<8>(PH, fb, geo, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, st); break;
+        }
+        if (rs != P2S_OK) return rs;
+    }
+    dim3 grid_a((max_a + 127) / 128, fb.n);
+    ProfScope pa(ctx, st, "fields_colour", cells * kModes * (kModes + 1), cells * (kModes + kAlphaStride) * 4);
+    colour_kernel<<<grid_a, 128, 0, st>>>(fb, geo, ctx->d_L);
+    P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+bool fields_group_ok(const p2s_ctx *ctx, int Fh, int Fw, int Ah_max, int Aw_max) {
+    int pitch = 0;
+    size_t smem = 0;
+    return ctx->field_method == 0 && field_kernel_fits(Fh, Fw, Ah_max, Aw_max, &pitch, &smem);
+}
+
+p2s_status launch_fields_group(p2s_ctx *ctx, int Fh, int Fw, const FrameBatch &fb, const FieldFrames &geo,
+                               cudaStream_t st) {
+    if (fb.n <= 0) return P2S_OK;
+    int ah_max = 0, aw_max = 0;
+    for (int k = 0; k < fb.n; ++k) {
+        ah_max = std::max(ah_max, geo.ah[k]);
+        aw_max = std::max(aw_max, geo.aw[k]);
+    }
+    int pitch = 0;
+    size_t fsmem = 0;
+    if (ctx->field_method != 0 || !field_kernel_fits(Fh, Fw, ah_max, aw_max, &pitch, &fsmem)) {
+        set_error("mixed anchor grids need the one-kernel Fourier filter");
+        return P2S_EINVAL;
+    }
+    return run_field_group(ctx, Fh, Fw, fb, geo, pitch, fsmem, st);
 }
 
 size_t fields_scratch_bytes(const FieldGeom &g, int n) {
@@ -545,6 +607,18 @@ p2s_status dense_prepare(p2s_ctx *ctx, const FieldGeom &g) {
 p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb, float *alpha, void *scratch,
                          cudaStream_t st) {
     if (fb.n <= 0) return P2S_OK;
+    // every frame on the same anchor grid: f [frame][mode][Ah][Aw] after the row-pass scratch,
+    // alpha [frame][Ah][Aw][kAlphaStride]
+    auto uniform_geo = [&](float *f) {
+        FieldFrames geo;
+        for (int k = 0; k < fb.n; ++k) {
+            geo.ah[k] = g.Ah;
+            geo.aw[k] = g.Aw;
+            geo.f[k] = f + (size_t)k * kModes * g.Ah * g.Aw;
+            geo.alpha[k] = alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride;
+        }
+        return geo;
+    };
     if (ctx->field_method == 1) {
         if (g.Ah > 128 || g.Aw > 128) {
             set_error("the dense anchor draw supports at most 128 anchors per axis");
@@ -568,7 +642,7 @@ p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb,
         dim3 grid_a((A + 127) / 128, fb.n);
         ProfScope pa(ctx, st, "fields_colour", (double)fb.n * A * kModes * (kModes + 1),
                      (double)fb.n * A * (kModes + kAlphaStride) * 4);
-        colour_kernel<<<grid_a, 128, 0, st>>>(fb, A, ctx->d_L, f, alpha);
+        colour_kernel<<<grid_a, 128, 0, st>>>(fb, uniform_geo(f), ctx->d_L);
         P2S_CUDA(cudaGetLastError());
         return P2S_OK;
     }
@@ -581,25 +655,7 @@ p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb,
     float *f = (float *)((char *)scratch + ((t_bytes + 255) & ~(size_t)255));
     int pitch = 0;
     size_t fsmem = 0;
-    if (field_kernel_fits(g, &pitch, &fsmem)) {
-        ProfScope pf(ctx, st, "fields_filter", 0.0, (double)fb.n * kModes * g.Ah * g.Aw * 4);
-        const int PW = g.Fw / 32, PH = g.Fh / 32;
-        p2s_status rs;
-        switch (PW) {
-            case 1: rs = launch_field_pw<1>(PH, g, fb, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, f, st); break;
-            case 2: rs = launch_field_pw<2>(PH, g, fb, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, f, st); break;
-            case 4: rs = launch_field_pw<4>(PH, g, fb, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, f, st); break;
-            default: rs = launch_field_pw<8>(PH, g, fb, pitch, fsmem, tw, th, ctx->d_kernel_of_mode, f, st); break;
-        }
-        if (rs != P2S_OK) return rs;
-        const int A = g.Ah * g.Aw;
-        dim3 grid_a((A + 127) / 128, fb.n);
-        ProfScope pa(ctx, st, "fields_colour", (double)fb.n * A * kModes * (kModes + 1),
-                     (double)fb.n * A * (kModes + kAlphaStride) * 4);
-        colour_kernel<<<grid_a, 128, 0, st>>>(fb, A, ctx->d_L, f, alpha);
-        P2S_CUDA(cudaGetLastError());
-        return P2S_OK;
-    }
+    if (field_kernel_fits(g, &pitch, &fsmem)) return run_field_group(ctx, g.Fh, g.Fw, fb, uniform_geo(f), pitch, fsmem, st);
 
     // rows: R row pairs per CTA, R * Fw <= kFftElems
     int R = kFftElems / g.Fw;
@@ -631,7 +687,7 @@ p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb,
     dim3 grid_a((A + 127) / 128, fb.n);
     ProfScope pa(ctx, st, "fields_colour", (double)fb.n * A * kModes * (kModes + 1),
                  (double)fb.n * A * (kModes + kAlphaStride) * 4);
-    colour_kernel<<<grid_a, 128, 0, st>>>(fb, A, ctx->d_L, f, alpha);
+    colour_kernel<<<grid_a, 128, 0, st>>>(fb, uniform_geo(f), ctx->d_L);
     P2S_CUDA(cudaGetLastError());
     return P2S_OK;
 }

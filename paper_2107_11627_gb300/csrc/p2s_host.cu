@@ -828,6 +828,19 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
         float *out;
     };
     std::vector<PostWarp> post_warp;
+    // one launch batch of frames of one shape: its buffers, for the stages after the fields
+    struct ShapeBatch {
+        FieldGeom g;
+        int C, nb;
+        FrameBatch fb;
+        float *alpha;
+        void *fscratch;
+        const float *ip[kMaxBatch];
+        float *xwm[kMaxBatch];
+        char *b16buf;
+        bool fields_done;
+    };
+    std::vector<ShapeBatch> batches;
     std::vector<char> done(n, 0);
     std::vector<int> idx;
     p2s_status st = P2S_OK;
@@ -869,11 +882,22 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             float *alpha = (float *)buf;
             float *xw = (float *)(buf + a_bytes + f_bytes);
             for (int k = 0; k < nb; ++k) xwm[k] = xw + (size_t)k * npx * C;
-            st = launch_fields(ctx, g, fb, alpha, buf + a_bytes, s);
             const bool bw = ctx->blur_then_warp;
-            if (st == P2S_OK && !bw) st = launch_warp(ctx, g, nb, ip, alpha, xwm, C, s);
             char *b16buf = buf + a_bytes + f_bytes + xw_bytes;
-            if (st == P2S_OK && split) st = launch_net16(ctx, g, nb, alpha, b16buf, 1, perm, ctx->d_status, s);
+            ShapeBatch sbt;
+            sbt.g = g;
+            sbt.C = C;
+            sbt.nb = nb;
+            sbt.fb = fb;
+            sbt.alpha = alpha;
+            sbt.fscratch = buf + a_bytes;
+            sbt.b16buf = b16buf;
+            sbt.fields_done = false;
+            for (int k = 0; k < nb; ++k) {
+                sbt.ip[k] = ip[k];
+                sbt.xwm[k] = xwm[k];
+            }
+            batches.push_back(sbt);
             for (int k = 0; k < nb; ++k) {
                 const int f = idx[i0 + k];
                 const float *a_k = alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride;
@@ -884,6 +908,55 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
                 if (split) b16[C == 3 ? 1 : 0].push_back(b16buf + (size_t)k * (f8 ? beta8_bytes(H, W, 1) : beta16_bytes(H, W, 1, perm)));
             }
         }
+    }
+    // ---- fields: frames of one torus in one launch, whatever their anchor grids ----
+    for (size_t b0 = 0; b0 < batches.size() && st == P2S_OK; ++b0) {
+        if (batches[b0].fields_done) continue;
+        const int Fh = batches[b0].g.Fh, Fw = batches[b0].g.Fw;
+        int ah_max = 0, aw_max = 0;
+        std::vector<size_t> same;
+        for (size_t b = b0; b < batches.size(); ++b)
+            if (!batches[b].fields_done && batches[b].g.Fh == Fh && batches[b].g.Fw == Fw) {
+                same.push_back(b);
+                ah_max = std::max(ah_max, batches[b].g.Ah);
+                aw_max = std::max(aw_max, batches[b].g.Aw);
+            }
+        if (same.size() > 1 && fields_group_ok(ctx, Fh, Fw, ah_max, aw_max)) {
+            FrameBatch fb;
+            FieldFrames geo;
+            fb.n = 0;
+            for (size_t b : same) {
+                ShapeBatch &sb = batches[b];
+                const FieldGeom &g = sb.g;
+                // the field block follows the row-pass scratch, as launch_fields lays it out
+                const size_t t_bytes = (size_t)sb.nb * kModes * g.Fh * g.Aw * sizeof(float);
+                float *f = (float *)((char *)sb.fscratch + ((t_bytes + 255) & ~(size_t)255));
+                for (int k = 0; k < sb.nb && st == P2S_OK; ++k) {
+                    fb.seed[fb.n] = sb.fb.seed[k];
+                    fb.scale[fb.n] = sb.fb.scale[k];
+                    geo.ah[fb.n] = g.Ah;
+                    geo.aw[fb.n] = g.Aw;
+                    geo.f[fb.n] = f + (size_t)k * kModes * g.Ah * g.Aw;
+                    geo.alpha[fb.n] = sb.alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride;
+                    if (++fb.n == kMaxBatch) {
+                        st = launch_fields_group(ctx, Fh, Fw, fb, geo, s);
+                        fb.n = 0;
+                    }
+                }
+                sb.fields_done = true;
+            }
+            if (st == P2S_OK && fb.n > 0) st = launch_fields_group(ctx, Fh, Fw, fb, geo, s);
+        } else {
+            ShapeBatch &sb = batches[b0];
+            st = launch_fields(ctx, sb.g, sb.fb, sb.alpha, sb.fscratch, s);
+            sb.fields_done = true;
+        }
+    }
+    // ---- warp and network per shape ----
+    for (ShapeBatch &sb : batches) {
+        if (st != P2S_OK) break;
+        if (!ctx->blur_then_warp) st = launch_warp(ctx, sb.g, sb.nb, sb.ip, sb.alpha, sb.xwm, sb.C, s);
+        if (st == P2S_OK && split) st = launch_net16(ctx, sb.g, sb.nb, sb.alpha, sb.b16buf, 1, perm, ctx->d_status, s);
     }
     for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
         if (tf[ci].empty()) continue;

@@ -51,6 +51,14 @@ struct FrameBatch {
     float scale[kMaxBatch];  // (D/r0)^(5/6), computed in FP64 on the host
 };
 
+// Per-frame anchor grids and output blocks of one field launch (frames of one torus):
+// f[k] is frame k's [kModes][ah][aw] filtered fields, alpha[k] its [ah][aw][kAlphaStride].
+struct FieldFrames {
+    int ah[kMaxBatch], aw[kMaxBatch];
+    float *f[kMaxBatch];
+    float *alpha[kMaxBatch];
+};
+
 // Device tables of the separable field filter for one torus length F.
 struct FilterTable {
     int F = 0;
@@ -173,6 +181,12 @@ p2s_status filter_table(p2s_ctx *ctx, int F, const FilterTable **out);
 // fields (k_fields.cu)
 p2s_status launch_noise(unsigned long long seed, int mode, int Fh, int Fw, float *out, cudaStream_t st);
 size_t fields_scratch_bytes(const FieldGeom &g, int n);
+// Fields of frames that share a torus (Fh, Fw) but not an anchor grid, in one launch of the
+// one-kernel Fourier filter and one of the colouring; fields_group_ok says whether that
+// filter serves the torus and the largest grids (else launch_fields per grid).
+bool fields_group_ok(const p2s_ctx *ctx, int Fh, int Fw, int Ah_max, int Aw_max);
+p2s_status launch_fields_group(p2s_ctx *ctx, int Fh, int Fw, const FrameBatch &fb, const FieldFrames &geo,
+                               cudaStream_t st);
 p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb, float *alpha, void *scratch,
                          cudaStream_t st);
 
