@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "p2s_internal.h"
@@ -49,17 +50,25 @@ constexpr int kGroups8 = 16;                    // FP8 beta: 8 hi + 8 lo groups 
 constexpr int kABytes = kTile * 128 * 2;        // A operand of one slot: [16 k-groups][128 rows][16 B]
 constexpr int kMaxItems = 6;
 
-struct Params {
+// One frame of a launch: its anchors ([Ah][Aw][36]), its beta block, its size, and the
+// index of its first unit (units run frame by frame, column block by column block, row-fastest).
+struct Frame {
     const float *alpha;
-    uint4 *beta16;
+    uint4 *beta;
+    int H, W, Aw, pitch, tiles_x, u0;
+};
+
+struct Params {
+    Frame fr[kMaxBatch];
+    int nf;
     const uint8_t *wstream;
     const float *bias;  // b1 [h1p], b2 [h2p]
     int *status;
-    int n, H, W, s, Ah, Aw;
+    int s;
     float inv_s;
-    int K, h1p, h2p, n3, ab_fmt, per, ones, perm, pitch;
+    int K, h1p, h2p, n3, ab_fmt, per, ones, perm;
     const float *scale8;  // non-null: write beta as E4M3 hi/lo pairs, beta_k multiplied by scale8[k]
-    int tiles_x, tiles_total, per_cta, nslots;
+    int tiles_total, per_cta, nslots;
     uint32_t wbytes, offA, offRow, rowBytes, offBias, offBar, offMisc;
     uint32_t item_off[kMaxItems], item_bytes[kMaxItems], item_n[kMaxItems], item_k[kMaxItems], item_soff[kMaxItems];
 };
@@ -77,19 +86,26 @@ struct UnitGeom {
     const float *a, *b;
 };
 
-__device__ __forceinline__ UnitGeom unit_geom(const Params &p, int u, int per_frame) {
+// the frame of unit u, searched forward from frame f (a slot's units only increase)
+__device__ __forceinline__ int frame_of(const Params &p, int u, int f) {
+    while (f + 1 < p.nf && u >= p.fr[f + 1].u0) ++f;
+    return f;
+}
+
+__device__ __forceinline__ UnitGeom unit_geom(const Params &p, int u, int f) {
     UnitGeom g;
-    g.f = u / per_frame;
-    const int rem = u - g.f * per_frame;
-    const int tcol = rem / p.H;
-    g.row = rem - tcol * p.H;
+    const Frame &F = p.fr[f];
+    g.f = f;
+    const int rem = u - F.u0;
+    const int tcol = rem / F.H;
+    g.row = rem - tcol * F.H;
     g.c0 = tcol * kTile;
     const int ay = g.row / p.s;
     g.fy = (float)(g.row - ay * p.s) * p.inv_s;
-    g.ax0 = min(g.c0, p.W - 1) / p.s;
-    g.nax = min(min(g.c0 + kTile - 1, p.W - 1) / p.s + 2, p.Aw) - g.ax0;
-    g.a = p.alpha + ((size_t)g.f * p.Ah * p.Aw + (size_t)ay * p.Aw + g.ax0) * kAlphaStride;
-    g.b = g.a + (size_t)p.Aw * kAlphaStride;
+    g.ax0 = min(g.c0, F.W - 1) / p.s;
+    g.nax = min(min(g.c0 + kTile - 1, F.W - 1) / p.s + 2, F.Aw) - g.ax0;
+    g.a = F.alpha + ((size_t)ay * F.Aw + g.ax0) * kAlphaStride;
+    g.b = g.a + (size_t)F.Aw * kAlphaStride;
     return g;
 }
 
@@ -193,27 +209,29 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
         const uint32_t dcol = tmem + ((uint32_t)(quad * 32) << 16) + 128u * slot;
         uint8_t *abuf = sm + p.offA + slot * kABytes;
         float *arow = (float *)(sm + p.offRow + slot * p.rowBytes);
-        const int per_frame = p.H * p.tiles_x;
-        // the two anchor rows of the slot's next unit, first kPre elements per thread,
-        // loaded while the current unit waits for its layer-1 result
-        float pa[kPre], pb[kPre];
+        // the slot's current frame (units increase along the loop)
+        int fcur = frame_of(p, u_base + slot, 0);
+        // the first kPre elements per thread of the slot's next unit's anchor row, interpolated
+        // at its image row: loaded and formed while the current unit waits for its layer-1 result
+        float pi[kPre];
         if (slot < n_local) {
-            const UnitGeom g = unit_geom(p, u_base + slot, per_frame);
+            const UnitGeom g = unit_geom(p, u_base + slot, fcur);
 #pragma unroll
             for (int q = 0; q < kPre; ++q) {
                 const int e2 = tid + 128 * q;
                 if (e2 < g.nax * kHiModes) {
                     const int off = anchor_off(e2);
-                    pa[q] = __ldg(g.a + off);
-                    pb[q] = __ldg(g.b + off);
+                    pi[q] = (1.0f - g.fy) * __ldg(g.a + off) + g.fy * __ldg(g.b + off);
                 }
             }
         }
         for (int i = slot; i < n_local; i += NS) {
             const uint32_t ph = (uint32_t)(i / NS) & 1u;
             const int u = u_base + i;
-            const UnitGeom g = unit_geom(p, u, per_frame);
-            const int f = g.f, row = g.row, c0 = g.c0;
+            fcur = frame_of(p, u, fcur);
+            const UnitGeom g = unit_geom(p, u, fcur);
+            const Frame &F = p.fr[fcur];
+            const int row = g.row, c0 = g.c0;
             const int col = c0 + m;
             bool ok = true;
             // ---- layer-1 operand: alpha_4..36 at (row, col), bilinear from the anchors.
@@ -227,14 +245,14 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
 #pragma unroll
                 for (int q = 0; q < kPre; ++q) {
                     const int e2 = tid + 128 * q;
-                    if (e2 < nax * kHiModes) arow[arow_idx(e2)] = (1.0f - fy) * pa[q] + fy * pb[q];
+                    if (e2 < nax * kHiModes) arow[arow_idx(e2)] = pi[q];
                 }
                 for (int e2 = tid + 128 * kPre; e2 < nax * kHiModes; e2 += 128) {
                     const int off = anchor_off(e2);
                     arow[arow_idx(e2)] = (1.0f - fy) * __ldg(g.a + off) + fy * __ldg(g.b + off);
                 }
                 ptx::named_bar(1 + slot, 128);
-                const int gj = min(col, p.W - 1);
+                const int gj = min(col, F.W - 1);
                 const int ax = gj / p.s - ax0;
                 const float fx = (float)(gj - (ax + ax0) * p.s) * p.inv_s;
                 const float4 *r0p = (const float4 *)(arow + ax * kRowStride);
@@ -270,14 +288,13 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                 if (lane == 0) ptx::mbar_arrive(BAR(barA(slot, 0)));
             }
             if (i + NS < n_local) {
-                const UnitGeom gn = unit_geom(p, u + NS, per_frame);
+                const UnitGeom gn = unit_geom(p, u + NS, frame_of(p, u + NS, fcur));
 #pragma unroll
                 for (int q = 0; q < kPre; ++q) {
                     const int e2 = tid + 128 * q;
                     if (e2 < gn.nax * kHiModes) {
                         const int off = anchor_off(e2);
-                        pa[q] = __ldg(gn.a + off);
-                        pb[q] = __ldg(gn.b + off);
+                        pi[q] = (1.0f - gn.fy) * __ldg(gn.a + off) + gn.fy * __ldg(gn.b + off);
                     }
                 }
             }
@@ -325,13 +342,13 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
             // ---- layer 3: beta (no bias) -> 16-bit groups of 8 in global memory ----
             ok = __all_sync(0xffffffffu, wait_bar(BAR(barD(slot, 2)), ph, ctl, 8) && ok);
             ptx::fence_after();
-            const bool store = ok && f < p.n && col < p.W;
+            const bool store = ok && col < F.W;
             const int pos = p.perm ? (col & ~31) + 8 * (col & 3) + ((col & 31) >> 2) : col;
             if (p.scale8) {
                 // FP8: k = 0 .. 127 (entries K, K + 1 are the bias columns, 1 before scaling, and
                 // k >= K + 2 have scale 0), 16 groups: hi bytes of k = 16 g .. 16 g + 15 in group g,
                 // lo bytes in group 8 + g
-                uint4 *dst8 = p.beta16 + ((size_t)(f * p.H + row) * kGroups8) * p.pitch + pos;
+                uint4 *dst8 = F.beta + ((size_t)row * kGroups8) * F.pitch + pos;
 #pragma unroll 1
                 for (int c32 = 0; ok && c32 < 128; c32 += 32) {
                     uint32_t d[32];
@@ -362,15 +379,15 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                                 }
                             }
                             const int g = c32 / 16 + q;
-                            dst8[(size_t)g * p.pitch] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                            dst8[(size_t)(8 + g) * p.pitch] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                            dst8[(size_t)g * F.pitch] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                            dst8[(size_t)(8 + g) * F.pitch] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                         }
                     }
                 }
                 ptx::fence_before();
                 continue;
             }
-            uint4 *dst = p.beta16 + ((size_t)(f * p.H + row) * kGroups) * p.pitch + pos;
+            uint4 *dst = F.beta + ((size_t)row * kGroups) * F.pitch + pos;
 #pragma unroll 1
             for (int c32 = 0; ok && c32 < 8 * kGroups; c32 += 32) {  // columns 112..127 are read, unused
                 uint32_t d[32];
@@ -398,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) net_kernel(const __grid_constant_
                             w4.y = pack2(v[2], v[3], FMT);
                             w4.z = pack2(v[4], v[5], FMT);
                             w4.w = pack2(v[6], v[7], FMT);
-                            dst[(size_t)g * p.pitch] = w4;
+                            dst[(size_t)g * F.pitch] = w4;
                         }
                     }
                 }
@@ -519,25 +536,45 @@ static int net_layout(const p2s_ctx *ctx, int s, int W, Params *p) {
     return (int)(p->offMisc + 16 + 1024);
 }
 
-p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones, int perm,
-                        int *status, cudaStream_t st) {
+p2s_status launch_net16_frames(p2s_ctx *ctx, const NetFrame *frames, int n, int ones, int perm, int *status,
+                               cudaStream_t st) {
     if (n <= 0) return P2S_OK;
+    if (n > kMaxBatch) {
+        set_error("network batch larger than %d frames", kMaxBatch);
+        return P2S_EINVAL;
+    }
     p2s_status s0 = tc_prepare(ctx);
     if (s0 != P2S_OK) return s0;
     Params p;
     std::memset(&p, 0, sizeof p);
-    p.alpha = alpha;
-    p.beta16 = (uint4 *)beta16;
+    p.scale8 = ctx->prec == P2S_FP8E4M3 ? ctx->tc.d_scale8 : nullptr;  // FP8: the hi/lo layout (perm 0)
+    if (p.scale8 && perm) {
+        set_error("the FP8 beta layout has natural column order");
+        return P2S_EUNSUPPORTED;
+    }
+    int units = 0, w_max = 1;
+    double npx = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const NetFrame &q = frames[i];
+        Frame &F = p.fr[i];
+        F.alpha = q.alpha;
+        F.beta = (uint4 *)q.beta;
+        F.H = q.H;
+        F.W = q.W;
+        F.Aw = (q.W - 1) / ctx->s + 2;
+        F.pitch = beta16_pitch(q.W, perm);
+        F.tiles_x = (q.W + kTile - 1) / kTile;
+        F.u0 = units;
+        units += F.tiles_x * q.H;
+        w_max = std::max(w_max, q.W);
+        npx += (double)q.H * q.W;
+    }
+    p.nf = n;
     p.wstream = (const uint8_t *)ctx->tc.d_H;
     p.bias = ctx->tc.d_bias;
     p.status = status;
-    p.n = n;
-    p.H = g.H;
-    p.W = g.W;
-    p.s = g.s;
-    p.Ah = g.Ah;
-    p.Aw = g.Aw;
-    p.inv_s = 1.0f / (float)g.s;
+    p.s = ctx->s;
+    p.inv_s = 1.0f / (float)ctx->s;
     p.K = ctx->K;
     p.h1p = ctx->tc.h1p;
     p.h2p = ctx->tc.h2p;
@@ -546,14 +583,8 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
     p.per = ctx->tc.split ? 2 : 1;
     p.ones = ones;
     p.perm = perm;
-    p.pitch = beta16_pitch(g.W, perm);
-    p.scale8 = ctx->prec == P2S_FP8E4M3 ? ctx->tc.d_scale8 : nullptr;  // FP8: the hi/lo layout (perm 0)
-    if (p.scale8 && perm) {
-        set_error("the FP8 beta layout has natural column order");
-        return P2S_EUNSUPPORTED;
-    }
-    p.tiles_x = (g.W + kTile - 1) / kTile;
-    p.tiles_total = p.tiles_x * g.H * n;
+    p.tiles_total = units;
+    if (units == 0) return P2S_OK;
     const Item16 *it = (const Item16 *)ctx->tc_items.data();
     uint32_t soff = 0;
     for (int i = 0; i < 3 * p.per; ++i) {
@@ -565,7 +596,7 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
         soff += it[i].bytes;
     }
     p.wbytes = soff;
-    const int smem = net_layout(ctx, g.s, g.W, &p);
+    const int smem = net_layout(ctx, ctx->s, w_max, &p);
     if (p.nslots < 1) {
         set_error("network weights too large for the tensor-core network kernel (%u B)", p.wbytes);
         return P2S_EUNSUPPORTED;
@@ -575,7 +606,6 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
     // contiguous runs of units per CTA (row-fastest order inside a column block)
     p.per_cta = (p.tiles_total + sms - 1) / sms;
     const int grid = (p.tiles_total + p.per_cta - 1) / p.per_cta;
-    const double npx = (double)g.H * g.W * n;
     double macs = 0.0;
     for (int l = 0; l < 3; ++l) macs += (double)ctx->dims[l] * ctx->dims[l + 1];
     ProfScope pr(ctx, st, "net_tc", 2.0 * macs * npx, npx * (p.scale8 ? kGroups8 : kGroups) * 16.0);
@@ -587,6 +617,21 @@ p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *al
         net_kernel<0><<<grid, 160 * p.nslots, smem, st>>>(p);
     }
     P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones, int perm,
+                        int *status, cudaStream_t st) {
+    const size_t fbytes = ctx->prec == P2S_FP8E4M3 ? beta8_bytes(g.H, g.W, 1) : beta16_bytes(g.H, g.W, 1, perm);
+    NetFrame fr[kMaxBatch];
+    for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+        const int nb = std::min(kMaxBatch, n - i0);
+        for (int k = 0; k < nb; ++k)
+            fr[k] = NetFrame{alpha + (size_t)(i0 + k) * g.Ah * g.Aw * kAlphaStride,
+                             (char *)beta16 + (size_t)(i0 + k) * fbytes, g.H, g.W};
+        p2s_status s0 = launch_net16_frames(ctx, fr, nb, ones, perm, status, st);
+        if (s0 != P2S_OK) return s0;
+    }
     return P2S_OK;
 }
 

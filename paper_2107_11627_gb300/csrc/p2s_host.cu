@@ -952,11 +952,26 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             sb.fields_done = true;
         }
     }
-    // ---- warp and network per shape ----
-    for (ShapeBatch &sb : batches) {
-        if (st != P2S_OK) break;
-        if (!ctx->blur_then_warp) st = launch_warp(ctx, sb.g, sb.nb, sb.ip, sb.alpha, sb.xwm, sb.C, s);
-        if (st == P2S_OK && split) st = launch_net16(ctx, sb.g, sb.nb, sb.alpha, sb.b16buf, 1, perm, ctx->d_status, s);
+    // ---- warp (per channel count) and network: up to kMaxBatch frames of any shapes per launch ----
+    {
+        std::vector<WarpFrame> wf[2];
+        std::vector<NetFrame> nf;
+        for (const ShapeBatch &sb : batches) {
+            const FieldGeom &g = sb.g;
+            const size_t fbytes = f8 ? beta8_bytes(g.H, g.W, 1) : beta16_bytes(g.H, g.W, 1, perm);
+            for (int k = 0; k < sb.nb; ++k) {
+                const float *a_k = sb.alpha + (size_t)k * g.Ah * g.Aw * kAlphaStride;
+                wf[sb.C == 3 ? 1 : 0].push_back(WarpFrame{sb.ip[k], sb.xwm[k], a_k, g.H, g.W});
+                nf.push_back(NetFrame{a_k, sb.b16buf + (size_t)k * fbytes, g.H, g.W});
+            }
+        }
+        for (int ci = 1; ci >= 0 && !ctx->blur_then_warp; --ci)
+            for (size_t i0 = 0; i0 < wf[ci].size() && st == P2S_OK; i0 += kMaxBatch)
+                st = launch_warp_frames(ctx, wf[ci].data() + i0, (int)std::min<size_t>(kMaxBatch, wf[ci].size() - i0),
+                                        ci ? 3 : 1, s);
+        for (size_t i0 = 0; split && i0 < nf.size() && st == P2S_OK; i0 += kMaxBatch)
+            st = launch_net16_frames(ctx, nf.data() + i0, (int)std::min<size_t>(kMaxBatch, nf.size() - i0), 1, perm,
+                                     ctx->d_status, s);
     }
     for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
         if (tf[ci].empty()) continue;

@@ -193,6 +193,14 @@ p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb,
 // warp (k_warp.cu)
 p2s_status launch_warp(const p2s_ctx *ctx, const FieldGeom &g, int n, const float *const *in, const float *alpha,
                        float *const *out, int C, cudaStream_t st);
+// The same over up to kMaxBatch frames of any sizes with C channels, in one launch.
+struct WarpFrame {
+    const float *in;
+    float *out;
+    const float *alpha;  // the frame's anchors, [Ah][Aw][36]
+    int H, W;
+};
+p2s_status launch_warp_frames(const p2s_ctx *ctx, const WarpFrame *frames, int n, int C, cudaStream_t st);
 
 // plain FP32 network and blur (k_simt.cu)
 p2s_status launch_mlp_simt(const p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, float *beta,
@@ -253,6 +261,15 @@ inline int beta16_pitch(int W, int perm) { return perm ? (W + 31) & ~31 : W; }
 size_t beta16_bytes(int H, int W, int n, int perm);
 p2s_status launch_net16(p2s_ctx *ctx, const FieldGeom &g, int n, const float *alpha, void *beta16, int ones, int perm,
                         int *status, cudaStream_t st);
+// The same over up to kMaxBatch frames of any sizes in one launch: frame i's anchors
+// ([Ah][Aw][36]) and its beta block (beta16_bytes or beta8_bytes of one frame).
+struct NetFrame {
+    const float *alpha;
+    void *beta;
+    int H, W;
+};
+p2s_status launch_net16_frames(p2s_ctx *ctx, const NetFrame *frames, int n, int ones, int perm, int *status,
+                               cudaStream_t st);
 // FP8 contexts: the network kernel writes beta as E4M3 hi/lo pairs in
 // [frame][row][16][col][16 B] (groups 0..7 the hi bytes of k = 16 g .. 16 g + 15,
 // groups 8..15 the lo bytes), column order natural (perm = 0).
