@@ -295,7 +295,7 @@ constexpr int kFieldWarps = 8;
 // Frames of one launch may differ in their anchor grids (one torus for all): each has its
 // own Ah x Aw and output block, and `pitch` is odd and at least every frame's Aw.
 template <int PW, int PH>
-__global__ void __launch_bounds__(32 * kFieldWarps, 1) field_kernel(FrameBatch fb, FieldFrames geo, int pitch,
+__global__ void __launch_bounds__(32 * kFieldWarps, (PW <= 4 && PH <= 4) ? 4 : 1) field_kernel(FrameBatch fb, FieldFrames geo, int pitch,
                                                                   const float2 *__restrict__ twx,
                                                                   const float *__restrict__ gainx,
                                                                   const float2 *__restrict__ twy,
@@ -380,27 +380,45 @@ __global__ void __launch_bounds__(32 * kFieldWarps, 1) field_kernel(FrameBatch f
 }
 
 // alpha(a) = (D/r0)^(5/6) L f(a): slot 0 (piston) = 0, slot l+1 = mode l + 2.
-__global__ void colour_kernel(FrameBatch fb, FieldFrames geo, const float *__restrict__ L) {
+// A block colours 128 consecutive anchors of one frame into shared memory (row pitch 37,
+// so that the per-anchor writes fall in distinct banks), then writes their alpha rows,
+// one contiguous run of 128 x 36 floats, with consecutive threads on consecutive floats.
+constexpr int kColourAnchors = 128;
+constexpr int kColourPitch = kAlphaStride + 1;
+
+__global__ void __launch_bounds__(kColourAnchors) colour_kernel(FrameBatch fb, FieldFrames geo,
+                                                                const float *__restrict__ L) {
     __shared__ float sL[kModes * kModes];
+    __shared__ float so[kColourAnchors * kColourPitch];
     for (int i = threadIdx.x; i < kModes * kModes; i += blockDim.x) sL[i] = L[i];
     __syncthreads();
     const int frame = blockIdx.y;
     const int A = geo.ah[frame] * geo.aw[frame];
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= A) return;
-    const float *ff = geo.f[frame] + a;
-    float v[kModes];
+    const int a0 = blockIdx.x * kColourAnchors;
+    if (a0 >= A) return;
+    const int na = min(kColourAnchors, A - a0);
+    const int t = threadIdx.x;
+    if (t < na) {
+        const float *ff = geo.f[frame] + a0 + t;
+        float v[kModes];
 #pragma unroll
-    for (int l = 0; l < kModes; ++l) v[l] = ff[(size_t)l * A];
-    const float sc = fb.scale[frame];
-    float *out = geo.alpha[frame] + (size_t)a * kAlphaStride;
-    out[0] = 0.0f;
+        for (int l = 0; l < kModes; ++l) v[l] = ff[(size_t)l * A];
+        const float sc = fb.scale[frame];
+        float *o = so + t * kColourPitch;
+        o[0] = 0.0f;
 #pragma unroll
-    for (int j = 0; j < kModes; ++j) {
-        float acc = 0.0f;
+        for (int j = 0; j < kModes; ++j) {
+            float acc = 0.0f;
 #pragma unroll
-        for (int l = 0; l <= j; ++l) acc = fmaf(sL[j * kModes + l], v[l], acc);
-        out[j + 1] = sc * acc;
+            for (int l = 0; l <= j; ++l) acc = fmaf(sL[j * kModes + l], v[l], acc);
+            o[j + 1] = sc * acc;
+        }
+    }
+    __syncthreads();
+    float *out = geo.alpha[frame] + (size_t)a0 * kAlphaStride;
+    for (int e = t; e < na * kAlphaStride; e += blockDim.x) {
+        const int a = e / kAlphaStride;
+        out[e] = so[a * kColourPitch + (e - a * kAlphaStride)];
     }
 }
 
@@ -476,9 +494,9 @@ static p2s_status run_field_group(p2s_ctx *ctx, int Fh, int Fw, const FrameBatch
         }
         if (rs != P2S_OK) return rs;
     }
-    dim3 grid_a((max_a + 127) / 128, fb.n);
+    dim3 grid_a((max_a + kColourAnchors - 1) / kColourAnchors, fb.n);
     ProfScope pa(ctx, st, "fields_colour", cells * kModes * (kModes + 1), cells * (kModes + kAlphaStride) * 4);
-    colour_kernel<<<grid_a, 128, 0, st>>>(fb, geo, ctx->d_L);
+    colour_kernel<<<grid_a, kColourAnchors, 0, st>>>(fb, geo, ctx->d_L);
     P2S_CUDA(cudaGetLastError());
     return P2S_OK;
 }
@@ -639,10 +657,10 @@ p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb,
                                                                            ctx->d_kernel_of_mode, f);
             P2S_CUDA(cudaGetLastError());
         }
-        dim3 grid_a((A + 127) / 128, fb.n);
+        dim3 grid_a((A + kColourAnchors - 1) / kColourAnchors, fb.n);
         ProfScope pa(ctx, st, "fields_colour", (double)fb.n * A * kModes * (kModes + 1),
                      (double)fb.n * A * (kModes + kAlphaStride) * 4);
-        colour_kernel<<<grid_a, 128, 0, st>>>(fb, uniform_geo(f), ctx->d_L);
+        colour_kernel<<<grid_a, kColourAnchors, 0, st>>>(fb, uniform_geo(f), ctx->d_L);
         P2S_CUDA(cudaGetLastError());
         return P2S_OK;
     }
@@ -684,10 +702,10 @@ p2s_status launch_fields(p2s_ctx *ctx, const FieldGeom &g, const FrameBatch &fb,
     P2S_CUDA(cudaGetLastError());
 
     const int A = g.Ah * g.Aw;
-    dim3 grid_a((A + 127) / 128, fb.n);
+    dim3 grid_a((A + kColourAnchors - 1) / kColourAnchors, fb.n);
     ProfScope pa(ctx, st, "fields_colour", (double)fb.n * A * kModes * (kModes + 1),
                  (double)fb.n * A * (kModes + kAlphaStride) * 4);
-    colour_kernel<<<grid_a, 128, 0, st>>>(fb, uniform_geo(f), ctx->d_L);
+    colour_kernel<<<grid_a, kColourAnchors, 0, st>>>(fb, uniform_geo(f), ctx->d_L);
     P2S_CUDA(cudaGetLastError());
     return P2S_OK;
 }
