@@ -809,16 +809,18 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
     return P2S_OK;
 }
 
-// Tensor-core gather: fields and warp per shape group, then ONE persistent
-// fused launch over every frame of the call (per channel count), whatever
-// their sizes; work is ordered frame by frame, tile by tile.
-static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, const p2s_image *out, int n,
-                                     const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s,
-                                     Scratch &sc) {
+// Tensor-core path: the fields once per filter torus, the warp and the network
+// over frames of any sizes (up to kMaxBatch per launch), then the blur: for the
+// gather form ONE persistent launch over every frame of the call (per channel
+// count), work ordered frame by frame, tile by tile; for the scatter form one
+// launch per shape batch.
+static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_image *out, int n,
+                              const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s, Scratch &sc) {
     std::vector<TcFrame> tf[2];      // C = 1, C = 3
     std::vector<const void *> b16[2];  // split form: each frame's beta16
-    const bool split = ctx->gather_split != 0;
-    const int perm = gather_perm(ctx->gather_split);  // the fragment kernels' beta layout
+    const bool scat = ctx->form == P2S_SCATTER;
+    const bool split = scat || ctx->gather_split != 0;
+    const int perm = scat ? 0 : gather_perm(ctx->gather_split);  // the fragment kernels' beta layout
     const bool f8 = ctx->prec == P2S_FP8E4M3;          // split kernel 1 with the FP8 layout
     struct PostWarp {
         FieldGeom g;
@@ -837,6 +839,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
         void *fscratch;
         const float *ip[kMaxBatch];
         float *xwm[kMaxBatch];
+        float *op[kMaxBatch];
         char *b16buf;
         bool fields_done;
     };
@@ -896,6 +899,7 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             for (int k = 0; k < nb; ++k) {
                 sbt.ip[k] = ip[k];
                 sbt.xwm[k] = xwm[k];
+                sbt.op[k] = out[idx[i0 + k]].data;
             }
             batches.push_back(sbt);
             for (int k = 0; k < nb; ++k) {
@@ -973,7 +977,18 @@ static p2s_status simulate_tc_gather(p2s_ctx *ctx, const p2s_image *frames, cons
             st = launch_net16_frames(ctx, nf.data() + i0, (int)std::min<size_t>(kMaxBatch, nf.size() - i0), 1, perm,
                                      ctx->d_status, s);
     }
-    for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
+    // scatter: one launch per shape batch (blur-then-warp: the input blurred into x_w)
+    for (size_t b = 0; scat && b < batches.size() && st == P2S_OK; ++b) {
+        const ShapeBatch &sb = batches[b];
+        const float *bin[kMaxBatch];
+        float *bout[kMaxBatch];
+        for (int k = 0; k < sb.nb; ++k) {
+            bin[k] = ctx->blur_then_warp ? sb.ip[k] : sb.xwm[k];
+            bout[k] = ctx->blur_then_warp ? sb.xwm[k] : sb.op[k];
+        }
+        st = launch_scatter_tc(ctx, sb.g.H, sb.g.W, sb.C, sb.nb, bin, bout, sb.b16buf, ctx->d_status, s);
+    }
+    for (int ci = 1; ci >= 0 && st == P2S_OK && !scat; --ci) {
         if (tf[ci].empty()) continue;
         const int C = ci ? 3 : 1;
         st = split ? launch_gather_blur(ctx, ctx->gather_split, tf[ci].data(), b16[ci].data(), (int)tf[ci].size(), C,
@@ -1009,8 +1024,26 @@ static p2s_status validate_simulate(p2s_ctx *ctx, const p2s_image *frames, int n
 
 static p2s_status simulate_impl(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
                                 const unsigned long long *seeds, const p2s_image *out, cudaStream_t s, Scratch &sc) {
-    if (tc_precision(ctx->prec) && ctx->form == P2S_GATHER)
-        return simulate_tc_gather(ctx, frames, out, n, d_over_r0, seeds, s, sc);
+    if (tc_precision(ctx->prec) && ctx->form == P2S_GATHER) return simulate_tc(ctx, frames, out, n, d_over_r0, seeds, s, sc);
+    if (tc_precision(ctx->prec) && ctx->form == P2S_SCATTER) {
+        // the path holds every frame's 16-bit beta at once: runs of frames with at most
+        // 4 GiB of it (at least one frame each)
+        const size_t cap = 4ull << 30;
+        for (int i0 = 0; i0 < n;) {
+            size_t bytes = 0;
+            int i1 = i0;
+            while (i1 < n) {
+                const size_t b = beta16_bytes(frames[i1].H, frames[i1].W, 1, 0);
+                if (i1 > i0 && bytes + b > cap) break;
+                bytes += b;
+                ++i1;
+            }
+            p2s_status st = simulate_tc(ctx, frames + i0, out + i0, i1 - i0, d_over_r0 + i0, seeds + i0, s, sc);
+            if (st != P2S_OK) return st;
+            i0 = i1;
+        }
+        return P2S_OK;
+    }
     // group frames of one shape, in order of first appearance
     std::vector<char> done(n, 0);
     std::vector<int> idx;
