@@ -82,29 +82,47 @@ static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 static_assert(kHSlot >= kGroups * kHRows * 16 && kHSlot % 1024 == 0, "basis slot");
 static_assert(kBetaRow % 1024 == 0, "beta slot alignment");
 
-struct Params {
-    CUtensorMap tmap_beta;  // (8, W, 14, H, n) 16-bit
-    CUtensorMap tmap_h;     // (8, 1104, 14) 16-bit
-    const float *xw[kMaxBatch];
-    float *y[kMaxBatch];
-    int *status;
-    int n, H, W, ab_fmt;
-    int seg, nseg, tiles_x, units;
+// One frame of a launch: its beta (tensor map (8, W, 14, H, 1), 16-bit), x_w and
+// output, size, segment rows, and the index of its first unit.  Frames of one
+// launch may differ in size.
+struct Frame {
+    CUtensorMap tmap_beta;
+    const float *xw;
+    float *y;
+    int H, W, seg, nseg, tiles_x, u0;
 };
+
+struct Params {
+    CUtensorMap tmap_h;  // (8, 1104, 14) 16-bit
+    Frame fr[kMaxBatch];
+    int *status;
+    int nf, ab_fmt, units;
+};
+
+static_assert(sizeof(Params) <= 32764, "kernel parameter limit");
 
 struct Unit {
-    int f, c0, s0, s1, npair;
+    int f, c0, s0, s1, npair, H, W;
 };
 
+// Units run frame by frame; within a frame segment by segment, strip by strip.
 __device__ __forceinline__ Unit unit_of(const Params &p, int u) {
-    const int per_frame = p.tiles_x * p.nseg;
+    int lo = 0, hi = p.nf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (u >= p.fr[mid].u0) lo = mid;
+        else hi = mid - 1;
+    }
+    const Frame &F = p.fr[lo];
     Unit r;
-    r.f = u / per_frame;
-    const int rem = u - r.f * per_frame;
-    const int sg = rem / p.tiles_x;
-    r.c0 = (rem - sg * p.tiles_x) * kStrip;
-    r.s0 = sg * p.seg;
-    r.s1 = min(p.H, r.s0 + p.seg);
+    r.f = lo;
+    r.H = F.H;
+    r.W = F.W;
+    const int rem = u - F.u0;
+    const int sg = rem / F.tiles_x;
+    r.c0 = (rem - sg * F.tiles_x) * kStrip;
+    r.s0 = sg * F.seg;
+    r.s1 = min(F.H, r.s0 + F.seg);
     r.npair = (r.s1 - r.s0 + 1) >> 1;
     return r;
 }
@@ -112,9 +130,9 @@ __device__ __forceinline__ Unit unit_of(const Params &p, int u) {
 // Write or add one finished (or partial) target row of this lane.
 template <int C>
 __device__ __forceinline__ void emit_row(const Params &p, const Unit &u, int col, int T, const float *v) {
-    if (T < 0 || T >= p.H || col >= p.W || T >= u.s1 + kHalo || T < u.s0 - kHalo) return;
-    const bool complete = (u.s0 == 0 || T - kHalo >= u.s0) && (u.s1 == p.H || T + kHalo < u.s1);
-    float *o = p.y[u.f] + ((size_t)T * p.W + col) * C;
+    if (T < 0 || T >= u.H || col >= u.W || T >= u.s1 + kHalo || T < u.s0 - kHalo) return;
+    const bool complete = (u.s0 == 0 || T - kHalo >= u.s0) && (u.s1 == u.H || T + kHalo < u.s1);
+    float *o = p.fr[u.f].y + ((size_t)T * u.W + col) * C;
     if (complete) {
 #pragma unroll
         for (int ch = 0; ch < C; ++ch) o[ch] = v[ch];
@@ -135,7 +153,7 @@ __device__ __forceinline__ void x_fetch(const Params &p, const Unit &u, int s, i
             const int i = e / (C * kPos), rem = e - i * (C * kPos);
             const int ch = rem / kPos, pos = rem - ch * kPos;
             const int row = s + i, col = u.c0 - kHalo + pos;
-            if (row < p.H && col >= 0 && col < p.W) v = __ldg(p.xw[u.f] + ((size_t)row * p.W + col) * C + ch);
+            if (row < u.H && col >= 0 && col < u.W) v = __ldg(p.fr[u.f].xw + ((size_t)row * u.W + col) * C + ch);
         }
         r[k] = v;
     }
@@ -322,8 +340,8 @@ __global__ void __launch_bounds__(kThreads, 1) scatter_kernel(const __grid_const
                 if (wait_bar(BAR(kBEmpty + slot), ((pc >> 1) & 1) ^ 1, ctl, 1)) {
                     ptx::mbar_arrive_tx(BAR(kBFull + slot), 2 * kBetaRow);
                     for (int i = 0; i < 2; ++i)
-                        ptx::tma_load_5d(sbase + kOffBeta + (2 * slot + i) * kBetaRow, &p.tmap_beta, 0, u.c0 - kHalo, 0,
-                                         u.s0 + 2 * pr + i, u.f, BAR(kBFull + slot));
+                        ptx::tma_load_5d(sbase + kOffBeta + (2 * slot + i) * kBetaRow, &p.fr[u.f].tmap_beta, 0,
+                                         u.c0 - kHalo, 0, u.s0 + 2 * pr + i, 0, BAR(kBFull + slot));
                 }
                 ++pc;
             };
@@ -502,9 +520,13 @@ int scatter_segment_rows(const p2s_ctx *ctx, int H) {
     return seg >= H ? ((H + 1) & ~1) : seg;
 }
 
-p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, float *const *y,
-                             const void *beta16, int *status, cudaStream_t st) {
-    if (n <= 0 || H <= 0 || W <= 0) return P2S_OK;
+p2s_status launch_scatter_frames(p2s_ctx *ctx, const ScatterFrame *frames, int n, int C, int *status,
+                                 cudaStream_t st) {
+    if (n <= 0) return P2S_OK;
+    if (n > kMaxBatch) {
+        set_error("scatter batch larger than %d frames", kMaxBatch);
+        return P2S_EINVAL;
+    }
     if (C != 1 && C != 3) {
         set_error("C must be 1 or 3");
         return P2S_EINVAL;
@@ -518,39 +540,47 @@ p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const flo
     Params p;
     std::memset(&p, 0, sizeof p);
     {
-        const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)kGroups, (cuuint64_t)H, (cuuint64_t)n};
-        const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * 16 * kGroups,
-                                       (cuuint64_t)W * 16 * kGroups * H};
-        const cuuint32_t box[5] = {8, kPos, kGroups, 1, 1};
-        s0 = encode(&p.tmap_beta, const_cast<void *>(beta16), 5, dims, strides, box);
-        if (s0 != P2S_OK) return s0;
-    }
-    {
         const cuuint64_t dims[3] = {8, (cuuint64_t)kHAll, (cuuint64_t)kGroups};
         const cuuint64_t strides[2] = {16, (cuuint64_t)kHAll * 16};
         const cuuint32_t box[3] = {8, kHRows, kGroups};
         s0 = encode(&p.tmap_h, ctx->tc.d_Hs, 3, dims, strides, box);
         if (s0 != P2S_OK) return s0;
     }
+    int units = 0;
+    double npx = 0.0;
     for (int i = 0; i < n; ++i) {
-        p.xw[i] = xw[i];
-        p.y[i] = y[i];
+        const ScatterFrame &q = frames[i];
+        if (q.H <= 0 || q.W <= 0) {
+            set_error("frame %d of the scatter batch is empty", i);
+            return P2S_EINVAL;
+        }
+        Frame &F = p.fr[i];
+        const cuuint64_t dims[5] = {8, (cuuint64_t)q.W, (cuuint64_t)kGroups, (cuuint64_t)q.H, 1};
+        const cuuint64_t strides[4] = {16, (cuuint64_t)q.W * 16, (cuuint64_t)q.W * 16 * kGroups,
+                                       (cuuint64_t)q.W * 16 * kGroups * q.H};
+        const cuuint32_t box[5] = {8, kPos, kGroups, 1, 1};
+        s0 = encode(&F.tmap_beta, const_cast<void *>(q.beta), 5, dims, strides, box);
+        if (s0 != P2S_OK) return s0;
+        F.xw = q.xw;
+        F.y = q.y;
+        F.H = q.H;
+        F.W = q.W;
+        F.seg = scatter_segment_rows(ctx, q.H);
+        F.nseg = (q.H + F.seg - 1) / F.seg;
+        F.tiles_x = (q.W + kStrip - 1) / kStrip;
+        F.u0 = units;
+        units += F.tiles_x * F.nseg;
+        npx += (double)q.H * q.W;
+        // rows that receive light from two segments are added into a zeroed output
+        if (F.nseg > 1) P2S_CUDA(cudaMemsetAsync(q.y, 0, (size_t)q.H * q.W * C * sizeof(float), st));
     }
     p.status = status;
-    p.n = n;
-    p.H = H;
-    p.W = W;
+    p.nf = n;
     p.ab_fmt = ctx->tc.fmt;
-    p.seg = scatter_segment_rows(ctx, H);
-    p.nseg = (H + p.seg - 1) / p.seg;
-    p.tiles_x = (W + kStrip - 1) / kStrip;
-    p.units = p.tiles_x * p.nseg * n;
-    if (p.nseg > 1)
-        for (int i = 0; i < n; ++i) P2S_CUDA(cudaMemsetAsync(y[i], 0, (size_t)H * W * C * sizeof(float), st));
+    p.units = units;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const int grid = p.units < sms ? p.units : sms;
-    const double npx = (double)H * W * n;
     ProfScope pr(ctx, st, "blur_tc_scatter", 2.0 * ctx->K * ctx->T * npx, npx * (C * 8.0 + kGroups * 16.0));
     if (C == 3) {
         P2S_CUDA(cudaFuncSetAttribute(scatter_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
@@ -560,6 +590,21 @@ p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const flo
         scatter_kernel<1><<<grid, kThreads, kSmemBytes, st>>>(p);
     }
     P2S_CUDA(cudaGetLastError());
+    return P2S_OK;
+}
+
+p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, float *const *y,
+                             const void *beta16, int *status, cudaStream_t st) {
+    if (n <= 0 || H <= 0 || W <= 0) return P2S_OK;
+    const size_t fbytes = beta16_bytes(H, W, 1, 0);
+    ScatterFrame fr[kMaxBatch];
+    for (int i0 = 0; i0 < n; i0 += kMaxBatch) {
+        const int nb = n - i0 < kMaxBatch ? n - i0 : kMaxBatch;
+        for (int k = 0; k < nb; ++k)
+            fr[k] = ScatterFrame{xw[i0 + k], y[i0 + k], (const char *)beta16 + (size_t)(i0 + k) * fbytes, H, W};
+        p2s_status s0 = launch_scatter_frames(ctx, fr, nb, C, status, st);
+        if (s0 != P2S_OK) return s0;
+    }
     return P2S_OK;
 }
 

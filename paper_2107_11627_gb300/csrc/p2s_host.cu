@@ -813,7 +813,7 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
 // over frames of any sizes (up to kMaxBatch per launch), then the blur: for the
 // gather form ONE persistent launch over every frame of the call (per channel
 // count), work ordered frame by frame, tile by tile; for the scatter form one
-// launch per shape batch.
+// launch per channel count and kMaxBatch frames of any sizes.
 static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_image *out, int n,
                               const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s, Scratch &sc) {
     std::vector<TcFrame> tf[2];      // C = 1, C = 3
@@ -977,16 +977,21 @@ static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_i
             st = launch_net16_frames(ctx, nf.data() + i0, (int)std::min<size_t>(kMaxBatch, nf.size() - i0), 1, perm,
                                      ctx->d_status, s);
     }
-    // scatter: one launch per shape batch (blur-then-warp: the input blurred into x_w)
-    for (size_t b = 0; scat && b < batches.size() && st == P2S_OK; ++b) {
-        const ShapeBatch &sb = batches[b];
-        const float *bin[kMaxBatch];
-        float *bout[kMaxBatch];
-        for (int k = 0; k < sb.nb; ++k) {
-            bin[k] = ctx->blur_then_warp ? sb.ip[k] : sb.xwm[k];
-            bout[k] = ctx->blur_then_warp ? sb.xwm[k] : sb.op[k];
+    // scatter: one launch per channel count and kMaxBatch frames of any sizes (blur-then-warp:
+    // the input blurred into x_w)
+    if (scat) {
+        std::vector<ScatterFrame> sf[2];
+        for (const ShapeBatch &sb : batches) {
+            const size_t fbytes = beta16_bytes(sb.g.H, sb.g.W, 1, 0);
+            for (int k = 0; k < sb.nb; ++k)
+                sf[sb.C == 3 ? 1 : 0].push_back(ScatterFrame{ctx->blur_then_warp ? sb.ip[k] : sb.xwm[k],
+                                                             ctx->blur_then_warp ? sb.xwm[k] : sb.op[k],
+                                                             sb.b16buf + (size_t)k * fbytes, sb.g.H, sb.g.W});
         }
-        st = launch_scatter_tc(ctx, sb.g.H, sb.g.W, sb.C, sb.nb, bin, bout, sb.b16buf, ctx->d_status, s);
+        for (int ci = 1; ci >= 0; --ci)
+            for (size_t i0 = 0; i0 < sf[ci].size() && st == P2S_OK; i0 += kMaxBatch)
+                st = launch_scatter_frames(ctx, sf[ci].data() + i0, (int)std::min<size_t>(kMaxBatch, sf[ci].size() - i0),
+                                           ci ? 3 : 1, ctx->d_status, s);
     }
     for (int ci = 1; ci >= 0 && st == P2S_OK && !scat; --ci) {
         if (tf[ci].empty()) continue;

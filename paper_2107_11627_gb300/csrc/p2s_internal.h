@@ -281,6 +281,16 @@ p2s_status launch_pack16(p2s_ctx *ctx, int H, int W, int n, const float *beta, v
 // Tensor-core scatter blur of n frames of one size from the 16-bit beta.
 p2s_status launch_scatter_tc(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, float *const *y,
                              const void *beta16, int *status, cudaStream_t st);
+// The same over up to kMaxBatch frames of any sizes with C channels in one launch: frame i's
+// x_w, output, and beta block (beta16_bytes of one frame, perm 0).
+struct ScatterFrame {
+    const float *xw;
+    float *y;
+    const void *beta;
+    int H, W;
+};
+p2s_status launch_scatter_frames(p2s_ctx *ctx, const ScatterFrame *frames, int n, int C, int *status,
+                                 cudaStream_t st);
 int scatter_segment_rows(const p2s_ctx *ctx, int H);
 // FFT evaluation of the scatter blur (FP32) from FP32 beta [n][H][W][K].
 p2s_status launch_blur_fft(p2s_ctx *ctx, int H, int W, int C, int n, const float *const *xw, const float *beta,
