@@ -1000,11 +1000,15 @@ static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_i
                                         ctx->d_status, s)
                    : launch_tc(ctx, kTcFull, tf[ci].data(), (int)tf[ci].size(), C, nullptr, nullptr, ctx->d_status, s);
     }
-    for (const PostWarp &w : post_warp) {
-        if (st != P2S_OK) break;
-        const float *in1[1] = {w.in};
-        float *out1[1] = {w.out};
-        st = launch_warp(ctx, w.g, 1, in1, w.alpha, out1, w.C, s);
+    // blur-then-warp: the blurred frames warped into the outputs, kMaxBatch frames of any
+    // sizes per launch and channel count
+    {
+        std::vector<WarpFrame> pw[2];
+        for (const PostWarp &w : post_warp) pw[w.C == 3 ? 1 : 0].push_back(WarpFrame{w.in, w.out, w.alpha, w.g.H, w.g.W});
+        for (int ci = 1; ci >= 0; --ci)
+            for (size_t i0 = 0; i0 < pw[ci].size() && st == P2S_OK; i0 += kMaxBatch)
+                st = launch_warp_frames(ctx, pw[ci].data() + i0, (int)std::min<size_t>(kMaxBatch, pw[ci].size() - i0),
+                                        ci ? 3 : 1, s);
     }
     sc.release();
     return st;

@@ -63,6 +63,30 @@ def test_uneven_batch_matches_oracle_and_is_batch_invariant():
         assert torch.equal(alone, ys[i])
 
 
+def test_uneven_scatter_batch_matches_oracle_and_frames_alone():
+    """The scatter form over mixed sizes and channel counts: one scatter launch per channel
+    count takes frames of several sizes (per-frame beta tensor maps and unit table).  Each
+    frame equals the oracle, and the frame simulated alone to 1e-6 (atomic adds where
+    segments meet may sum in another order); 16-row segments give several segments per
+    frame, so those adds run."""
+    sim = _sim(form="scatter")
+    sim.set_option("scatter_segment_rows", 16)
+    shapes = [(40, 72), (33, 130), (64, 64), (40, 72), (20, 200)]
+    xs = _frames(shapes) + [inputs.blob_image(36, 50, 1, 2150), inputs.blob_image(50, 36, 1, 2151)]
+    dr = [0.6 + 0.7 * i for i in range(len(xs))]
+    seeds = [700 + i for i in range(len(xs))]
+    ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
+    sim.check()
+    for i in (1, 4, 5):
+        ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
+                                    CorrParams(8, (16.0,)), (33, 33), form="scatter")
+        close(ys[i].cpu().numpy(), ref.y, TOL_BF16, i)
+    for i in range(len(xs)):
+        (alone,) = sim.simulate([torch.from_numpy(xs[i]).cuda()], [dr[i]], [seeds[i]])
+        sim.check()
+        close(ys[i].cpu().numpy(), alone.cpu().numpy(), 1e-6, i)
+
+
 @pytest.mark.parametrize("form", ["gather", "scatter"])
 def test_graph_mode_matches_plain_launches(form):
     shapes = [(96, 160), (64, 64), (96, 160), (130, 70)]
