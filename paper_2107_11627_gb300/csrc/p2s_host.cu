@@ -809,15 +809,33 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
     return P2S_OK;
 }
 
+// The host entry point's schedule for the gather form (warp then blur): frames
+// [bounds[k], bounds[k + 1]) form chunk k, whose inputs are on the device once
+// in_ready[k] completes; out_done[k] is recorded once its outputs are written.
+// The fields and the network, which read no input pixels, run first over all
+// frames; then each chunk's warp and blur, alternating between the call's stream
+// and `aux` (if set).
+struct Pipeline {
+    int nch;
+    const int *bounds;
+    const cudaEvent_t *in_ready;
+    const cudaEvent_t *out_done;
+    cudaStream_t aux;
+    cudaEvent_t prefix_done, aux_done;
+};
+
 // Tensor-core path: the fields once per filter torus, the warp and the network
 // over frames of any sizes (up to kMaxBatch per launch), then the blur: for the
 // gather form ONE persistent launch over every frame of the call (per channel
 // count), work ordered frame by frame, tile by tile; for the scatter form one
-// launch per channel count and kMaxBatch frames of any sizes.
+// launch per channel count and kMaxBatch frames of any sizes.  With a Pipeline
+// (gather form, warp then blur) the warp and the blur go chunk by chunk instead.
 static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_image *out, int n,
-                              const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s, Scratch &sc) {
+                              const float *d_over_r0, const unsigned long long *seeds, cudaStream_t s, Scratch &sc,
+                              const Pipeline *pl = nullptr) {
     std::vector<TcFrame> tf[2];      // C = 1, C = 3
     std::vector<const void *> b16[2];  // split form: each frame's beta16
+    std::vector<int> tf_idx[2];        // each entry's frame index in the call
     const bool scat = ctx->form == P2S_SCATTER;
     const bool split = scat || ctx->gather_split != 0;
     const int perm = scat ? 0 : gather_perm(ctx->gather_split);  // the fragment kernels' beta layout
@@ -840,6 +858,7 @@ static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_i
         const float *ip[kMaxBatch];
         float *xwm[kMaxBatch];
         float *op[kMaxBatch];
+        int fidx[kMaxBatch];
         char *b16buf;
         bool fields_done;
     };
@@ -900,6 +919,7 @@ static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_i
                 sbt.ip[k] = ip[k];
                 sbt.xwm[k] = xwm[k];
                 sbt.op[k] = out[idx[i0 + k]].data;
+                sbt.fidx[k] = idx[i0 + k];
             }
             batches.push_back(sbt);
             for (int k = 0; k < nb; ++k) {
@@ -908,6 +928,7 @@ static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_i
                 // blur-then-warp: the fused launch blurs the input into x_w, a warp follows
                 tf[C == 3 ? 1 : 0].push_back(
                     TcFrame{bw ? ip[k] : xwm[k], bw ? xwm[k] : out[f].data, a_k, H, W, g.Ah, g.Aw, 0, 0, 0});
+                tf_idx[C == 3 ? 1 : 0].push_back(f);
                 if (bw) post_warp.push_back(PostWarp{g, C, xwm[k], a_k, out[f].data});
                 if (split) b16[C == 3 ? 1 : 0].push_back(b16buf + (size_t)k * (f8 ? beta8_bytes(H, W, 1) : beta16_bytes(H, W, 1, perm)));
             }
@@ -969,13 +990,65 @@ static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_i
                 nf.push_back(NetFrame{a_k, sb.b16buf + (size_t)k * fbytes, g.H, g.W});
             }
         }
-        for (int ci = 1; ci >= 0 && !ctx->blur_then_warp; --ci)
+        for (int ci = 1; ci >= 0 && !ctx->blur_then_warp && !pl; --ci)
             for (size_t i0 = 0; i0 < wf[ci].size() && st == P2S_OK; i0 += kMaxBatch)
                 st = launch_warp_frames(ctx, wf[ci].data() + i0, (int)std::min<size_t>(kMaxBatch, wf[ci].size() - i0),
                                         ci ? 3 : 1, s);
         for (size_t i0 = 0; split && i0 < nf.size() && st == P2S_OK; i0 += kMaxBatch)
             st = launch_net16_frames(ctx, nf.data() + i0, (int)std::min<size_t>(kMaxBatch, nf.size() - i0), 1, perm,
                                      ctx->d_status, s);
+    }
+    if (pl && st == P2S_OK) {
+        // chunk by chunk: the chunk's inputs, its warp, its blur (the fields and the network
+        // of every frame are queued above on s)
+        P2S_CUDA(cudaEventRecord(pl->prefix_done, s));
+        bool used_aux = false;
+        for (int k = 0; k < pl->nch && st == P2S_OK; ++k) {
+            const int i0 = pl->bounds[k], i1 = pl->bounds[k + 1];
+            cudaStream_t cs = (pl->aux && (k & 1)) ? pl->aux : s;
+            if (cs != s) {
+                P2S_CUDA(cudaStreamWaitEvent(cs, pl->prefix_done, 0));
+                used_aux = true;
+            }
+            P2S_CUDA(cudaStreamWaitEvent(cs, pl->in_ready[k], 0));
+            std::vector<WarpFrame> wk;
+            for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
+                wk.clear();
+                for (const ShapeBatch &sb : batches) {
+                    if (sb.C != (ci ? 3 : 1)) continue;
+                    for (int j = 0; j < sb.nb; ++j)
+                        if (sb.fidx[j] >= i0 && sb.fidx[j] < i1)
+                            wk.push_back(WarpFrame{sb.ip[j], sb.xwm[j],
+                                                   sb.alpha + (size_t)j * sb.g.Ah * sb.g.Aw * kAlphaStride, sb.g.H,
+                                                   sb.g.W});
+                }
+                for (size_t w0 = 0; w0 < wk.size() && st == P2S_OK; w0 += kMaxBatch)
+                    st = launch_warp_frames(ctx, wk.data() + w0, (int)std::min<size_t>(kMaxBatch, wk.size() - w0),
+                                            ci ? 3 : 1, cs);
+            }
+            for (int ci = 1; ci >= 0 && st == P2S_OK; --ci) {
+                std::vector<TcFrame> tk;
+                std::vector<const void *> bk;
+                for (size_t q = 0; q < tf[ci].size(); ++q)
+                    if (tf_idx[ci][q] >= i0 && tf_idx[ci][q] < i1) {
+                        tk.push_back(tf[ci][q]);
+                        if (split) bk.push_back(b16[ci][q]);
+                    }
+                if (tk.empty()) continue;
+                const int C = ci ? 3 : 1;
+                st = split ? launch_gather_blur(ctx, ctx->gather_split, tk.data(), bk.data(), (int)tk.size(), C,
+                                                ctx->d_status, cs)
+                           : launch_tc(ctx, kTcFull, tk.data(), (int)tk.size(), C, nullptr, nullptr, ctx->d_status, cs);
+            }
+            if (st == P2S_OK) P2S_CUDA(cudaEventRecord(pl->out_done[k], cs));
+        }
+        // scratch is released on s: after the other stream's chunks
+        if (used_aux) {
+            cudaEventRecord(pl->aux_done, pl->aux);
+            cudaStreamWaitEvent(s, pl->aux_done, 0);
+        }
+        sc.release();
+        return st;
     }
     // scatter: one launch per channel count and kMaxBatch frames of any sizes (blur-then-warp:
     // the input blurred into x_w)
@@ -1338,7 +1411,7 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
     // mode keeps one stream: its captured launches share the context's scratch arena.
     const bool two = nch > 1 && !ctx->use_graphs;
     if (two && !ctx->aux_stream) P2S_CUDA(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
-    while ((int)ctx->host_ev.size() < 2 * nch + 3) {
+    while ((int)ctx->host_ev.size() < 2 * nch + 5) {
         cudaEvent_t e;
         P2S_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ctx->host_ev.push_back(e);
@@ -1376,14 +1449,32 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
         }
         if (st == P2S_OK && cudaEventRecord(ctx->host_ev[2 + 2 * k], cin) != cudaSuccess) st = P2S_ECUDA;
     }
-    // the path per chunk on the caller's stream, each chunk's results copied back
+    // The tensor-core gather (warp then blur, no graphs): the fields and the network of every
+    // frame first, while the inputs arrive (they read no input pixels), then each chunk's warp
+    // and blur once its inputs are in.  Otherwise the whole path per chunk.
+    const bool piped = !ctx->use_graphs && tc_precision(ctx->prec) && ctx->form == P2S_GATHER && !ctx->blur_then_warp;
+    if (piped && st == P2S_OK) {
+        std::vector<cudaEvent_t> in_ready(nch), out_done(nch);
+        for (int k = 0; k < nch; ++k) {
+            in_ready[k] = ctx->host_ev[2 + 2 * k];
+            out_done[k] = ctx->host_ev[3 + 2 * k];
+        }
+        const Pipeline pl{nch, bounds.data(), in_ready.data(), out_done.data(), two ? ctx->aux_stream : nullptr,
+                          ctx->host_ev[3 + 2 * nch], ctx->host_ev[4 + 2 * nch]};
+        Scratch sc{ctx, s, false};
+        st = simulate_tc(ctx, din.data(), dout.data(), n, d_over_r0, seeds, s, sc, &pl);
+        sc.release();
+    }
+    // the path per chunk (or, piped, only the copies back), each chunk's results copied back
     for (int k = 0; k < nch && st == P2S_OK; ++k) {
         const int i0 = chunk_begin(k), i1 = chunk_begin(k + 1);
-        cudaStream_t cs = (two && (k & 1)) ? ctx->aux_stream : s;
-        P2S_CUDA(cudaStreamWaitEvent(cs, ctx->host_ev[2 + 2 * k], 0));
-        st = p2s_simulate(ctx, din.data() + i0, i1 - i0, d_over_r0 + i0, seeds + i0, dout.data() + i0, (void *)cs);
-        if (st != P2S_OK) break;
-        P2S_CUDA(cudaEventRecord(ctx->host_ev[3 + 2 * k], cs));
+        if (!piped) {
+            cudaStream_t cs = (two && (k & 1)) ? ctx->aux_stream : s;
+            P2S_CUDA(cudaStreamWaitEvent(cs, ctx->host_ev[2 + 2 * k], 0));
+            st = p2s_simulate(ctx, din.data() + i0, i1 - i0, d_over_r0 + i0, seeds + i0, dout.data() + i0, (void *)cs);
+            if (st != P2S_OK) break;
+            P2S_CUDA(cudaEventRecord(ctx->host_ev[3 + 2 * k], cs));
+        }
         P2S_CUDA(cudaStreamWaitEvent(cout, ctx->host_ev[3 + 2 * k], 0));
         for (int i = i0; i < i1; ++i) {
             const size_t bytes = (size_t)out[i].H * out[i].W * out[i].C * 4;

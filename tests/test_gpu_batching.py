@@ -251,10 +251,13 @@ def test_split_gather_blur_then_warp_and_graphs(split_kernel):
 def test_host_entry_point_pipelines_chunks_bit_exact():
     """p2s_simulate_host splits >= 32 frames into chunks whose copies overlap the path of the
     neighbouring chunks; every frame must equal the device-buffer call (the gather is
-    batch-invariant), including a chunk boundary inside a run of equal shapes."""
+    batch-invariant), including a chunk boundary inside a run of equal shapes and chunks
+    that mix channel counts."""
     sim = _sim()
     shapes = [(48, 64)] * 20 + [(40, 72)] * 17 + [(64, 48)] * 3
     xs = _frames(shapes, first=2600)
+    xs[21:21] = [inputs.blob_image(36, 50, 1, 2690)]
+    xs.append(inputs.blob_image(50, 36, 1, 2691))
     dr = [0.5 + 0.1 * i for i in range(len(xs))]
     seeds = [900 + i for i in range(len(xs))]
     yd = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
