@@ -156,9 +156,12 @@ p2s_status p2s_simulate(p2s_ctx *ctx, const p2s_image *frames, int n, const floa
  * device->host copy the path of the chunk after, on two copy streams owned by
  * the context.  The chunks' paths alternate between `stream` and a second
  * compute stream owned by the context (one stream in graph mode), so that a
- * chunk's kernels fill the SMs the previous chunk's last wave leaves idle.
- * Results equal p2s_simulate's.  Pinned host memory gives full copy bandwidth
- * and overlap. */
+ * chunk's kernels fill the SMs the previous chunk's last wave leaves idle.  On
+ * the tensor-core gather form (warp then blur, graphs off) the anchor fields
+ * and the network (Sec. 3.3-3.4), which read no input pixels, run for every
+ * frame first, while the inputs are copied in; each chunk then runs only its
+ * warp and blur.  Results equal p2s_simulate's.  Pinned host memory gives full
+ * copy bandwidth and overlap. */
 p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const float *d_over_r0,
                              const unsigned long long *seeds, const p2s_image *out, void *stream);
 
