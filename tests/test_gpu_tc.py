@@ -138,6 +138,27 @@ def test_tc_full_size_frame_fp16():
     close(y.cpu().numpy(), ref.y, TOL_BF16)
 
 
+def test_benchmark_batch_64_frames_512_rgb():
+    """The benchmark's launch configuration: 64 RGB frames of 512 x 512 in one call (one field,
+    warp, network and packed-FP16 gather launch over all of them, D/r0 spread over [1, 5]).
+    The first and the last frame are checked whole against the oracle, and both equal the
+    same frame simulated alone, bit for bit."""
+    sim = _sim("fp16")
+    n = 64
+    xs = [inputs.blob_image(512, 512, 3, 3000 + i) for i in range(n)]
+    dr = [1.0 + 4.0 * i / (n - 1) for i in range(n)]
+    seeds = [2 * 10**6 + i for i in range(n)]
+    ys = sim.simulate([torch.from_numpy(x).cuda() for x in xs], dr, seeds)
+    sim.check()
+    for i in (0, n - 1):
+        ref = oracle.frame.simulate(xs[i].astype(np.float64), seeds[i], dr[i], cfg2()["H"], cfg2()["layers"],
+                                    CorrParams(8, (16.0,)), (33, 33), form="gather")
+        close(ys[i].cpu().numpy(), ref.y, TOL_BF16, i)
+        (alone,) = sim.simulate([torch.from_numpy(xs[i]).cuda()], [dr[i]], [seeds[i]])
+        sim.check()
+        assert torch.equal(alone, ys[i]), i
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("c,h,w", [(3, 48, 160), (1, 37, 150)])
 def test_tc_blur_stage_h2_rounding_points(prec, c, h, w):
