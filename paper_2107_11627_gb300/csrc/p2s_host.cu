@@ -1,5 +1,6 @@
 // Host side of libp2s: the C ABI, context set-up in FP64, validation, dispatch.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -815,6 +816,9 @@ static p2s_status simulate_group(p2s_ctx *ctx, const p2s_image *frames, const p2
 // The fields and the network, which read no input pixels, run first over all
 // frames; then each chunk's warp and blur, alternating between the call's stream
 // and `aux` (if set).
+// issue_inputs (if set) queues the input copies and records in_ready[]; it is called once
+// the fields and the network are queued, so that their launches do not wait behind the
+// copies' host-side submission.
 struct Pipeline {
     int nch;
     const int *bounds;
@@ -822,6 +826,7 @@ struct Pipeline {
     const cudaEvent_t *out_done;
     cudaStream_t aux;
     cudaEvent_t prefix_done, aux_done;
+    std::function<p2s_status()> issue_inputs;
 };
 
 // Tensor-core path: the fields once per filter torus, the warp and the network
@@ -1002,6 +1007,7 @@ static p2s_status simulate_tc(p2s_ctx *ctx, const p2s_image *frames, const p2s_i
         // chunk by chunk: the chunk's inputs, its warp, its blur (the fields and the network
         // of every frame are queued above on s)
         P2S_CUDA(cudaEventRecord(pl->prefix_done, s));
+        if (pl->issue_inputs) st = pl->issue_inputs();
         bool used_aux = false;
         for (int k = 0; k < pl->nch && st == P2S_OK; ++k) {
             const int i0 = pl->bounds[k], i1 = pl->bounds[k + 1];
@@ -1438,29 +1444,39 @@ p2s_status p2s_simulate_host(p2s_ctx *ctx, const p2s_image *frames, int n, const
     }
     auto chunk_begin = [&](int k) { return bounds[k]; };
     // all host->device copies, chunk by chunk, each chunk's end marked
-    for (int k = 0; k < nch && st == P2S_OK; ++k) {
-        for (int i = chunk_begin(k); i < chunk_begin(k + 1); ++i) {
-            const size_t bytes = (size_t)frames[i].H * frames[i].W * frames[i].C * 4;
-            if (cudaMemcpyAsync(din[i].data, frames[i].data, bytes, cudaMemcpyHostToDevice, cin) != cudaSuccess) {
-                set_error("host->device copy failed");
-                st = P2S_ECUDA;
-                break;
+    auto copy_in = [&]() -> p2s_status {
+        for (int k = 0; k < nch; ++k) {
+            for (int i = chunk_begin(k); i < chunk_begin(k + 1); ++i) {
+                const size_t bytes = (size_t)frames[i].H * frames[i].W * frames[i].C * 4;
+                if (cudaMemcpyAsync(din[i].data, frames[i].data, bytes, cudaMemcpyHostToDevice, cin) != cudaSuccess) {
+                    set_error("host->device copy failed");
+                    return P2S_ECUDA;
+                }
             }
+            if (cudaEventRecord(ctx->host_ev[2 + 2 * k], cin) != cudaSuccess) return P2S_ECUDA;
         }
-        if (st == P2S_OK && cudaEventRecord(ctx->host_ev[2 + 2 * k], cin) != cudaSuccess) st = P2S_ECUDA;
-    }
+        return P2S_OK;
+    };
     // The tensor-core gather (warp then blur, no graphs): the fields and the network of every
-    // frame first, while the inputs arrive (they read no input pixels), then each chunk's warp
-    // and blur once its inputs are in.  Otherwise the whole path per chunk.
+    // frame first, the input copies queued right after them (they read no input pixels), then
+    // each chunk's warp and blur once its inputs are in.  Otherwise the copies first and the
+    // whole path per chunk.
     const bool piped = !ctx->use_graphs && tc_precision(ctx->prec) && ctx->form == P2S_GATHER && !ctx->blur_then_warp;
+    if (!piped) st = copy_in();
     if (piped && st == P2S_OK) {
         std::vector<cudaEvent_t> in_ready(nch), out_done(nch);
         for (int k = 0; k < nch; ++k) {
             in_ready[k] = ctx->host_ev[2 + 2 * k];
             out_done[k] = ctx->host_ev[3 + 2 * k];
         }
-        const Pipeline pl{nch, bounds.data(), in_ready.data(), out_done.data(), two ? ctx->aux_stream : nullptr,
-                          ctx->host_ev[3 + 2 * nch], ctx->host_ev[4 + 2 * nch]};
+        const Pipeline pl{nch,
+                          bounds.data(),
+                          in_ready.data(),
+                          out_done.data(),
+                          two ? ctx->aux_stream : nullptr,
+                          ctx->host_ev[3 + 2 * nch],
+                          ctx->host_ev[4 + 2 * nch],
+                          copy_in};
         Scratch sc{ctx, s, false};
         st = simulate_tc(ctx, din.data(), dout.data(), n, d_over_r0, seeds, s, sc, &pl);
         sc.release();
